@@ -1,0 +1,151 @@
+/*
+ * mmot.h -- C ABI of the GB300 library for multi-marginal optimal transport
+ * with pairwise L1 cost (arXiv 2405.19246, "A numerical algorithm with linear
+ * complexity for Multi-marginal Optimal Transport with L1 Cost").
+ *
+ * Problem (Sec. 2 for l = 3, Sec. 4.2 for general l):
+ *   l discrete marginals; marginal k has N_k support points x_k (sorted,
+ *   nondecreasing, any spacing) and weights mu_k >= 0 with sum mu_k = 1.
+ *   Cost      c(y_1..y_l) = sum_{p<q} |y_p - y_q|.
+ *   Kernel    K = exp(-c/eps).
+ *   Plan      t = prod_k phi_k(i_k) K                     (Eq. k-marginal T value)
+ *   Sinkhorn  phi_j <- mu_j / M_j, j = 1..l in order      (Sec. 4.2 update formulas)
+ *   with the marginal product (tensor-vector product)
+ *             M_j(i) = sum over the other marginals' points of
+ *                      prod_{m != j} phi_m K               (Eq. Jk k margin)
+ *   computed in O(sum_k N_k) work by the paper's separated summations
+ *   (Sec. 3, Sec. 4.2) instead of the O(prod N_k) contraction.
+ *
+ * Potentials.  The library stores g_k = eps ln phi_k (FP64).  The paper's dual
+ * variables are alpha_k = -g_k - eps/l (Sec. 2, definition of phi).  A zero
+ * weight gives g = -inf.  Initial potentials are phi = 1/N_k (Algorithm 1,
+ * line 1), i.e. g_k = -eps ln N_k.
+ *
+ * Conventions for every call:
+ *   - Calls never throw and never abort; they return an mmot_status.  On an
+ *     error mmot_last_error() gives a message (thread-local).
+ *   - Pointers marked "host or device" may point to host memory or to device
+ *     memory of the plan's GPU; the library detects which.
+ *   - The plan copies every input into device memory it owns; caller buffers
+ *     are never retained.  Output buffers are caller-owned.
+ *   - Work is issued on the stream given to mmot_plan_create (borrowed, not
+ *     owned; NULL = the legacy default stream).  Calls that return values to
+ *     host memory synchronise that stream before returning.
+ */
+#ifndef MMOT_H
+#define MMOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mmot_plan_s *mmot_plan; /* opaque, owned by the library */
+
+typedef enum {
+    MMOT_OK = 0,
+    MMOT_ERR_INVALID_ARG = 1,  /* bad size, eps, marginal index, weights      */
+    MMOT_ERR_UNSORTED = 2,     /* a support x_k is not nondecreasing          */
+    MMOT_ERR_OOM = 3,          /* device allocation failed                    */
+    MMOT_ERR_CUDA = 4,         /* a CUDA runtime call failed                  */
+    MMOT_ERR_TIMEOUT = 5,      /* a bounded inter-tile wait gave up           */
+    MMOT_ERR_NOT_CONVERGED = 6,/* itr_max reached with residual > tol         */
+    MMOT_ERR_NONFINITE = 7,    /* a product or potential became NaN or inf    */
+    MMOT_ERR_RANGE = 8         /* input outside the supported range           */
+} mmot_status;
+
+typedef enum {
+    MMOT_FP64 = 0,               /* all scan arithmetic in FP64                  */
+    MMOT_FP32_SCAN_FP64_POT = 1  /* FP32 in-tile scans, FP64 log-domain carries,
+                                    FP64 potentials, residual and objective     */
+} mmot_precision;
+
+typedef struct {
+    int iters;        /* Sinkhorn iterations performed (one = l updates)        */
+    double residual;  /* sum over marginals 1..l-1 of ||phi_k . M_k - mu_k||_1
+                         after the last iteration (Algorithm 1 / 4, line 7)      */
+    double W;         /* <C, T> of the regularised plan (Eq. k-mmot distance)    */
+    double primal;    /* <C,T> + eps <T, ln T> = sum_k <g_k, marg_k>             */
+    double dual;      /* sum_k <g_k, mu_k> + eps - eps Z                         */
+    double mass;      /* Z = sum of all plan entries                             */
+} mmot_result;
+
+/* Create a plan (Sec. 4.2 problem statement; Algorithm 1 inputs).
+ *   l      number of marginals, 2 <= l <= 8.
+ *   N      host array of l sizes, N[k] >= 1, sum N[k] < 2^31.
+ *   x      l pointers (host or device, see inputs_on_device) to N[k] FP64
+ *          support points each, nondecreasing (else MMOT_ERR_UNSORTED).
+ *   mu     l pointers to N[k] FP64 weights, >= 0, each summing to 1 within
+ *          1e-9 (else MMOT_ERR_INVALID_ARG).  Zero weights are allowed.
+ *   eps    entropic regularisation, > 0 and finite.
+ *   prec   MMOT_FP64 or MMOT_FP32_SCAN_FP64_POT.
+ *   inputs_on_device  0: x and mu are host pointers; 1: device pointers.
+ *   cuda_stream       cudaStream_t to issue work on (borrowed).
+ *   out    receives the plan; *out is NULL on failure.
+ * Merges the supports into one order by (x, k, index) (the tie rule of the
+ * order classes D_p, Eq. D_p), tiles it, and sets g_k = -eps ln N_k. */
+mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x,
+                             const double *const *mu, double eps, mmot_precision prec,
+                             int inputs_on_device, void *cuda_stream, mmot_plan *out);
+
+/* Marginal product of marginal k with the current potentials (Eq. Jk k margin,
+ * computed as in Sec. 3.1 / Sec. 4.2):
+ *   plan_marginal = 0: out[i] = M_k(i)
+ *   plan_marginal = 1: out[i] = phi_k(i) M_k(i)   (the k-th marginal of the plan)
+ *   plan_marginal = 2: out[i] = ln M_k(i)
+ * out: N[k] FP64 values, host or device.  Potentials are not changed. */
+mmot_status mmot_marginal(mmot_plan p, int k, int plan_marginal, double *out);
+
+/* Run n_iters Gauss-Seidel Sinkhorn iterations (Sec. 4.2 update formulas;
+ * Algorithm 4 loop body): for j = 1..l, g_j <- eps (ln mu_j - ln M_j).
+ * If residual_out is not NULL it receives the residual of Algorithm 1 line 7
+ * (sum over marginals 1..l-1 of ||phi_k . M_k - mu_k||_1) after the last
+ * iteration, which costs l-1 extra marginal products. */
+mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out);
+
+/* Solve: iterate while t < itr_max and residual > tol (Algorithm 1 loop), the
+ * residual being evaluated every `check_every` iterations (mmot_set_option),
+ * then evaluate the objective terms (Eq. k-mmot distance).  tol <= 0 runs
+ * exactly itr_max iterations.  Returns MMOT_ERR_NOT_CONVERGED (with out
+ * filled) when itr_max is reached with residual > tol > 0. */
+mmot_status mmot_solve(mmot_plan p, double tol, int itr_max, mmot_result *out);
+
+/* Objective terms for the current potentials (residual over all l marginals,
+ * W, primal, dual, mass); iters is left 0. */
+mmot_status mmot_objective(mmot_plan p, mmot_result *out);
+
+/* Copy potentials g_k = eps ln phi_k (N[k] FP64, host or device) out of or
+ * into the plan: warm start and checkpoint/resume. */
+mmot_status mmot_get_potentials(mmot_plan p, int k, double *g_out);
+mmot_status mmot_set_potentials(mmot_plan p, int k, const double *g_in);
+
+/* Plan options (integers):
+ *   MMOT_OPT_CHECK_EVERY   residual evaluation period in mmot_solve (default 10)
+ *   MMOT_OPT_SPIN_LIMIT    inter-tile wait limit in polls (default ~1 s)
+ *   MMOT_OPT_USE_GRAPH     capture the per-iteration launches in a CUDA graph (default 1) */
+enum { MMOT_OPT_CHECK_EVERY = 1, MMOT_OPT_SPIN_LIMIT = 2, MMOT_OPT_USE_GRAPH = 3 };
+mmot_status mmot_set_option(mmot_plan p, int option, int64_t value);
+
+/* Plan information: number of tiles, points per tile, total points, kernel
+ * launches per Sinkhorn iteration. */
+typedef struct {
+    int64_t total_points;
+    int64_t tiles;
+    int tile_points;
+    int threads_per_block;
+    int launches_per_iteration;
+    int precision;
+} mmot_plan_info;
+mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
+
+/* Destroy a plan; NULL-safe. */
+void mmot_destroy(mmot_plan p);
+
+/* Message of the last error on this thread ("" if none). */
+const char *mmot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMOT_H */

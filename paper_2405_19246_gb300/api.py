@@ -1,0 +1,141 @@
+"""Python face of the C ABI (``include/mmot.h``): one :class:`Plan` per problem.
+
+Inputs may be numpy arrays (host) or CUDA torch tensors (device); outputs are
+numpy arrays unless a CUDA ``out`` tensor is given.  PyTorch is used only for
+device memory and streams.  All computation happens in ``libmmot_gb300.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+
+_PREC = {"fp64": nat.MMOT_FP64, "fp32": nat.MMOT_FP32_SCAN_FP64_POT}
+_KIND = {"M": 0, "plan": 1, "lnM": 2}
+
+
+def _is_cuda_tensor(a):
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(a, torch.Tensor) and a.is_cuda
+
+
+def _host_f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Plan:
+    """An l-marginal L1-cost entropic OT instance resident on the GPU.
+
+    xs, mus: sequences of l supports (sorted) and weights (sum 1); all numpy
+    (host) or all CUDA float64 tensors (device).  eps > 0.  precision "fp32"
+    (FP32 in-tile scans, FP64 carries and potentials) or "fp64".
+    """
+
+    def __init__(self, xs, mus, eps, precision="fp32", stream=None):
+        self.l = len(xs)
+        if len(mus) != self.l:
+            raise ValueError("xs and mus differ in length")
+        on_dev = _is_cuda_tensor(xs[0])
+        keep = []
+        if on_dev:
+            import torch
+            xs = [x.to(torch.float64).contiguous() for x in xs]
+            mus = [m.to(torch.float64).contiguous() for m in mus]
+            xp = [x.data_ptr() for x in xs]
+            mp = [m.data_ptr() for m in mus]
+            Ns = [x.numel() for x in xs]
+            keep = xs + mus
+        else:
+            xs = [_host_f64(x) for x in xs]
+            mus = [_host_f64(m) for m in mus]
+            xp = [x.ctypes.data for x in xs]
+            mp = [m.ctypes.data for m in mus]
+            Ns = [len(x) for x in xs]
+            keep = xs + mus
+        self.N = Ns
+        self.eps = float(eps)
+        self.precision = precision
+        N_arr = (ctypes.c_int64 * self.l)(*Ns)
+        X = (ctypes.c_void_p * self.l)(*xp)
+        M = (ctypes.c_void_p * self.l)(*mp)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        nat.check(nat.lib().mmot_plan_create(self.l, N_arr, X, M, self.eps, _PREC[precision],
+                                             1 if on_dev else 0, st, ctypes.byref(h)))
+        del keep
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().mmot_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -----------------------------------------------------------
+    def marginal(self, k, kind="M", out=None):
+        """M_k (kind "M"), phi_k M_k ("plan") or ln M_k ("lnM")."""
+        if out is None:
+            res = np.empty(self.N[k], dtype=np.float64)
+            nat.check(nat.lib().mmot_marginal(self._h, k, _KIND[kind], res.ctypes.data))
+            return res
+        nat.check(nat.lib().mmot_marginal(self._h, k, _KIND[kind], out.data_ptr()))
+        return out
+
+    def sinkhorn_step(self, n_iters=1, residual=False):
+        r = ctypes.c_double(np.nan)
+        nat.check(nat.lib().mmot_sinkhorn_step(self._h, int(n_iters),
+                                               ctypes.byref(r) if residual else None))
+        return r.value if residual else None
+
+    def solve(self, tol, itr_max, allow_not_converged=True):
+        res = nat.MmotResult()
+        st = nat.lib().mmot_solve(self._h, float(tol), int(itr_max), ctypes.byref(res))
+        if not (st == nat.MMOT_OK or (allow_not_converged and st == 6)):
+            nat.check(st)
+        return dict(iters=res.iters, residual=res.residual, W=res.W, primal=res.primal,
+                    dual=res.dual, mass=res.mass, converged=(st == nat.MMOT_OK))
+
+    def objective(self):
+        res = nat.MmotResult()
+        nat.check(nat.lib().mmot_objective(self._h, ctypes.byref(res)))
+        return dict(residual=res.residual, W=res.W, primal=res.primal, dual=res.dual, mass=res.mass)
+
+    def get_potentials(self, k, out=None):
+        if out is None:
+            g = np.empty(self.N[k], dtype=np.float64)
+            nat.check(nat.lib().mmot_get_potentials(self._h, k, g.ctypes.data))
+            return g
+        nat.check(nat.lib().mmot_get_potentials(self._h, k, out.data_ptr()))
+        return out
+
+    def set_potentials(self, k, g):
+        if _is_cuda_tensor(g):
+            nat.check(nat.lib().mmot_set_potentials(self._h, k, g.contiguous().data_ptr()))
+        else:
+            g = _host_f64(g)
+            nat.check(nat.lib().mmot_set_potentials(self._h, k, g.ctypes.data))
+
+    def set_option(self, option, value):
+        nat.check(nat.lib().mmot_set_option(self._h, int(option), int(value)))
+
+    def info(self):
+        inf = nat.MmotPlanInfo()
+        nat.check(nat.lib().mmot_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}

@@ -1,0 +1,755 @@
+// C ABI and host runtime of the GB300 l-marginal L1 Sinkhorn library
+// (arXiv 2405.19246).  See include/mmot.h for the contract of every call.
+//
+// Plan layout in device memory (one plan = one problem instance):
+//   merged order of all T = sum_k N_k points (Eq. D_p tie rule), struct of arrays
+//     pos   FP32 [T]  (x_t - x_first_of_tile)/eps   (FP64 in the all-FP64 path)
+//     mid   u8   [T]  marginal of the point
+//     lphi  FP32 [T]  g_m(i)/eps - beta[tile][m]  (re-centred ln phi, Algorithm 5 idea;
+//                     FP64 in the all-FP64 path)
+//   per tile: first index, first/last x (FP64), span, per-marginal counts before
+//     the tile, reference tile for each marginal's baseline, baselines beta (FP64)
+//   per marginal: g_k (FP64 potentials), mu_k and ln mu_k (FP64)
+//   scan scratch: per-tile aggregates / inclusive prefixes / flags, backward
+//     carries, residual partial sums.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mmot.h"
+#include "mmot_internal.cuh"
+#include "shapes.cuh"
+
+using namespace mmot;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mmot_status fail(mmot_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? MMOT_ERR_OOM : MMOT_ERR_CUDA,       \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Kahan-compensated sum of per-tile partial sums (one block).
+__global__ void k_sum_partials(const double *partial, int n, double *out, int accumulate)
+{
+    __shared__ double s_sum[256];
+    __shared__ double s_c[256];
+    double sum = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double y = partial[i] - c;
+        const double t = sum + y;
+        c = (t - sum) - y;
+        sum = t;
+    }
+    s_sum[threadIdx.x] = sum;
+    s_c[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, Cc = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            const double y = s_sum[i] - s_c[i] - Cc;
+            const double t = S + y;
+            Cc = (t - S) - y;
+            S = t;
+        }
+        out[0] = accumulate ? out[0] + S : S;
+    }
+}
+
+}  // namespace
+
+struct mmot_plan_s {
+    int l = 0;
+    int64_t N[MMOT_MAXL] = {0};
+    int64_t T = 0;
+    double eps = 0;
+    int prec = 1;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int nt = 0;
+    int NB = 0;
+    int NS = 0;
+    int K = 0;
+    int NT = 0;
+    int check_every = 10;
+    int spin_limit = 1 << 23;
+    int use_graph = 1;
+    // host copies needed to re-centre potentials
+    std::vector<uint8_t> h_mid;
+    std::vector<uint32_t> h_tile_of;   // tile of each merged point
+    std::vector<uint32_t> h_mpos[MMOT_MAXL];  // merged index of each local point
+    std::vector<uint32_t> h_tstart;
+    std::vector<int32_t> h_reftile;
+    std::vector<double> h_beta;
+    // device
+    void *pos = nullptr;     // FP32 or FP64 (esz bytes per point)
+    uint8_t *mid = nullptr;
+    void *lphi = nullptr;    // FP32 or FP64
+    size_t esz = 4;
+    uint32_t *tstart = nullptr;
+    double *xlb = nullptr, *xrb = nullptr;
+    double *span = nullptr;
+    int32_t *cnt = nullptr, *reftile = nullptr;
+    double *beta = nullptr;
+    double *g[MMOT_MAXL] = {nullptr};
+    double *lnmu[MMOT_MAXL] = {nullptr};
+    double *mu[MMOT_MAXL] = {nullptr};
+    double *agg = nullptr, *inc = nullptr, *bcarry = nullptr, *partial = nullptr;
+    int *flags = nullptr;   // flags followed by the tile counter
+    size_t flags_bytes = 0;
+    int *err = nullptr;
+    double *dsum = nullptr;  // reduction results
+    double *scratch = nullptr;  // max N doubles
+    cudaGraphExec_t graph = nullptr;
+    std::vector<void *> allocs;
+
+    ~mmot_plan_s()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (void *p : allocs) cudaFree(p);
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+
+    template <typename Tp>
+    cudaError_t alloc(Tp **p, size_t n)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(1, n) * sizeof(Tp));
+        if (e == cudaSuccess) {
+            allocs.push_back(q);
+            *p = static_cast<Tp *>(q);
+        }
+        return e;
+    }
+};
+
+namespace {
+
+template <int NB>
+cudaError_t launch_pair_nb(const SweepArgs &a, bool fp64, cudaStream_t st, bool fwd)
+{
+    if (fp64) return fwd ? launch_fwd<NB, double>(a, st) : launch_bwd<NB, double>(a, st);
+    return fwd ? launch_fwd<NB, float>(a, st) : launch_bwd<NB, float>(a, st);
+}
+
+cudaError_t launch_sweep(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, bool fwd)
+{
+    switch (NB) {
+    case 1: return launch_pair_nb<1>(a, fp64, st, fwd);
+    case 2: return launch_pair_nb<2>(a, fp64, st, fwd);
+    case 3: return launch_pair_nb<3>(a, fp64, st, fwd);
+    case 4: return launch_pair_nb<4>(a, fp64, st, fwd);
+    case 5: return launch_pair_nb<5>(a, fp64, st, fwd);
+    case 6: return launch_pair_nb<6>(a, fp64, st, fwd);
+    case 7: return launch_pair_nb<7>(a, fp64, st, fwd);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NB>
+void shape_nb(bool fp64, int *K, int *NT)
+{
+    if (fp64) {
+        *K = Shape<NB, double>::K;
+        *NT = Shape<NB, double>::NT;
+    } else {
+        *K = Shape<NB, float>::K;
+        *NT = Shape<NB, float>::NT;
+    }
+}
+
+void shape_of(int NB, bool fp64, int *K, int *NT)
+{
+    switch (NB) {
+    case 1: shape_nb<1>(fp64, K, NT); break;
+    case 2: shape_nb<2>(fp64, K, NT); break;
+    case 3: shape_nb<3>(fp64, K, NT); break;
+    case 4: shape_nb<4>(fp64, K, NT); break;
+    case 5: shape_nb<5>(fp64, K, NT); break;
+    case 6: shape_nb<6>(fp64, K, NT); break;
+    default: shape_nb<7>(fp64, K, NT); break;
+    }
+}
+
+SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
+{
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.l = p->l;
+    a.j = j;
+    a.nt = p->nt;
+    a.mode = mode;
+    a.spin_limit = p->spin_limit;
+    a.eps = p->eps;
+    a.tstart = p->tstart;
+    a.xlb = p->xlb;
+    a.xrb = p->xrb;
+    a.span = p->span;
+    a.cnt = p->cnt;
+    a.reftile = p->reftile;
+    a.beta = p->beta;
+    a.pos = p->pos;
+    a.mid = p->mid;
+    a.lphi = p->lphi;
+    a.agg = p->agg;
+    a.inc = p->inc;
+    a.flags = p->flags;
+    a.counter = p->flags + (size_t)p->nt * (p->NB + 1);
+    a.bcarry = p->bcarry;
+    a.gj = p->g[j];
+    a.lnmuj = p->lnmu[j];
+    a.muj = p->mu[j];
+    a.out = out;
+    a.partial = p->partial;
+    a.err = p->err;
+    return a;
+}
+
+// One marginal product pass for target j: backward scan, then forward scan
+// with combine and epilogue.
+mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out)
+{
+    const SweepArgs a = make_args(p, j, mode, out);
+    const bool fp64 = (p->prec == MMOT_FP64);
+    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
+    CUDA_TRY(launch_sweep(p->NB, a, fp64, p->st, false));
+    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
+    CUDA_TRY(launch_sweep(p->NB, a, fp64, p->st, true));
+    return MMOT_OK;
+}
+
+mmot_status enqueue_iteration(mmot_plan p)
+{
+    for (int j = 0; j < p->l; ++j) {
+        mmot_status s = enqueue_product(p, j, MODE_UPDATE, nullptr);
+        if (s != MMOT_OK) return s;
+    }
+    return MMOT_OK;
+}
+
+mmot_status check_device_error(mmot_plan p)
+{
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    if (h) {
+        CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
+        if (h & ERR_TIMEOUT) return fail(MMOT_ERR_TIMEOUT, "an inter-tile wait reached its poll limit");
+        if (h & ERR_RANGE) return fail(MMOT_ERR_RANGE, "a tile exceeded its target-point capacity");
+        if (h & ERR_NONFINITE) return fail(MMOT_ERR_NONFINITE, "a potential became NaN or infinite");
+    }
+    return MMOT_OK;
+}
+
+// residual of marginals [k0, k1) into p->dsum[0]
+mmot_status enqueue_residual(mmot_plan p, int k0, int k1)
+{
+    CUDA_TRY(cudaMemsetAsync(p->dsum, 0, sizeof(double), p->st));
+    for (int k = k0; k < k1; ++k) {
+        mmot_status s = enqueue_product(p, k, MODE_RESIDUAL, nullptr);
+        if (s != MMOT_OK) return s;
+        k_sum_partials<<<1, 256, 0, p->st>>>(p->partial, p->nt, p->dsum, 1);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return MMOT_OK;
+}
+
+mmot_status read_scalar(mmot_plan p, const double *d, double *h)
+{
+    CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    return MMOT_OK;
+}
+
+// Re-centre the merged-order copy of ln phi_k after g_k changed on the host side.
+mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
+{
+    const int l = p->l;
+    const int nt = p->nt;
+    std::vector<double> bmax(nt, -INFINITY);
+    for (int64_t i = 0; i < p->N[k]; ++i) {
+        const uint32_t t = p->h_mpos[k][i];
+        const uint32_t b = p->h_tile_of[t];
+        bmax[b] = std::max(bmax[b], g[i] / p->eps);
+    }
+    for (int b = 0; b < nt; ++b) {
+        double v = bmax[b];
+        if (!std::isfinite(v)) v = 0.0;
+        p->h_beta[(size_t)b * l + k] = v;
+    }
+    // lphi for the points of marginal k, written as one full upload of lphi
+    std::vector<unsigned char> lp((size_t)p->T * p->esz);
+    CUDA_TRY(cudaMemcpyAsync(lp.data(), p->lphi, lp.size(), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    for (int64_t i = 0; i < p->N[k]; ++i) {
+        const uint32_t t = p->h_mpos[k][i];
+        const uint32_t b = p->h_tile_of[t];
+        const double v = g[i] / p->eps - p->h_beta[(size_t)b * l + k];
+        if (p->esz == 8)
+            reinterpret_cast<double *>(lp.data())[t] = v;
+        else
+            reinterpret_cast<float *>(lp.data())[t] = (float)v;
+    }
+    // the device beta of other marginals may have moved: read them back first
+    std::vector<double> hb((size_t)nt * l);
+    CUDA_TRY(cudaMemcpyAsync(hb.data(), p->beta, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    for (int b = 0; b < nt; ++b) hb[(size_t)b * l + k] = p->h_beta[(size_t)b * l + k];
+    CUDA_TRY(cudaMemcpyAsync(p->beta, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, p->st));
+    CUDA_TRY(cudaMemcpyAsync(p->lphi, lp.data(), lp.size(), cudaMemcpyHostToDevice, p->st));
+    CUDA_TRY(cudaMemcpyAsync(p->g[k], g.data(), sizeof(double) * p->N[k], cudaMemcpyHostToDevice, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    return MMOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mmot_last_error(void) { return g_last_error.c_str(); }
+
+void mmot_destroy(mmot_plan p)
+{
+    if (!p) return;
+    if (p->st) cudaStreamSynchronize(p->st);
+    delete p;
+}
+
+mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, const double *const *mu,
+                             double eps, mmot_precision prec, int inputs_on_device, void *cuda_stream,
+                             mmot_plan *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(MMOT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (l < 2 || l > MMOT_MAXL) return fail(MMOT_ERR_INVALID_ARG, "l = %d outside [2, 8]", l);
+    if (!N || !x || !mu) return fail(MMOT_ERR_INVALID_ARG, "N, x or mu is NULL");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MMOT_ERR_INVALID_ARG, "eps must be positive and finite");
+    if (prec != MMOT_FP64 && prec != MMOT_FP32_SCAN_FP64_POT)
+        return fail(MMOT_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    int64_t T = 0;
+    for (int k = 0; k < l; ++k) {
+        if (N[k] < 1) return fail(MMOT_ERR_INVALID_ARG, "N[%d] = %lld < 1", k, (long long)N[k]);
+        if (!x[k] || !mu[k]) return fail(MMOT_ERR_INVALID_ARG, "x[%d] or mu[%d] is NULL", k, k);
+        T += N[k];
+    }
+    if (T >= (int64_t)1 << 31) return fail(MMOT_ERR_RANGE, "sum N = %lld too large", (long long)T);
+
+    // ---- inputs to host, validation -------------------------------------
+    std::vector<std::vector<double>> hx(l), hmu(l);
+    for (int k = 0; k < l; ++k) {
+        hx[k].resize(N[k]);
+        hmu[k].resize(N[k]);
+        const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        CUDA_TRY(cudaMemcpy(hx[k].data(), x[k], sizeof(double) * N[k], kind));
+        CUDA_TRY(cudaMemcpy(hmu[k].data(), mu[k], sizeof(double) * N[k], kind));
+        for (int64_t i = 0; i < N[k]; ++i) {
+            if (!std::isfinite(hx[k][i])) return fail(MMOT_ERR_INVALID_ARG, "x[%d][%lld] not finite", k, (long long)i);
+            if (i > 0 && hx[k][i] < hx[k][i - 1])
+                return fail(MMOT_ERR_UNSORTED, "x[%d] decreases at index %lld", k, (long long)i);
+        }
+        long double s = 0.0L;
+        for (int64_t i = 0; i < N[k]; ++i) {
+            const double m = hmu[k][i];
+            if (!(m >= 0.0) || !std::isfinite(m))
+                return fail(MMOT_ERR_INVALID_ARG, "mu[%d][%lld] negative or not finite", k, (long long)i);
+            s += m;
+        }
+        if (std::fabs((double)s - 1.0) > 1e-9)
+            return fail(MMOT_ERR_INVALID_ARG, "mu[%d] sums to %.17g, not 1", k, (double)s);
+    }
+
+    mmot_plan p = new (std::nothrow) mmot_plan_s();
+    if (!p) return fail(MMOT_ERR_OOM, "host allocation failed");
+    p->l = l;
+    p->T = T;
+    p->eps = eps;
+    p->prec = (int)prec;
+    for (int k = 0; k < l; ++k) p->N[k] = N[k];
+    p->NB = l - 1;
+    p->NS = 1 << p->NB;
+    const bool fp64 = (prec == MMOT_FP64);
+    shape_of(p->NB, fp64, &p->K, &p->NT);
+    if (cuda_stream) {
+        p->st = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete p;
+            return fail(MMOT_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
+        }
+        p->own_stream = true;
+    }
+
+    // ---- merged order by (x, k, i) ----------------------------------------
+    std::vector<double> xm(T);
+    p->h_mid.resize(T);
+    for (int k = 0; k < l; ++k) p->h_mpos[k].resize(N[k]);
+    {
+        std::vector<int64_t> head(l, 0);
+        for (int64_t t = 0; t < T; ++t) {
+            int best = -1;
+            for (int k = 0; k < l; ++k) {
+                if (head[k] >= N[k]) continue;
+                if (best < 0 || hx[k][head[k]] < hx[best][head[best]]) best = k;
+            }
+            xm[t] = hx[best][head[best]];
+            p->h_mid[t] = (uint8_t)best;
+            p->h_mpos[best][head[best]] = (uint32_t)t;
+            head[best] += 1;
+        }
+    }
+
+    // ---- tiles: at most K points, span * max_s w_s <= limit --------------
+    double wmax = 0.0;
+    for (int s = 0; s <= l; ++s) wmax = std::max(wmax, (double)s * (l - s));
+    const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
+    std::vector<uint32_t> &ts = p->h_tstart;
+    ts.clear();
+    {
+        int64_t t = 0;
+        while (t < T) {
+            ts.push_back((uint32_t)t);
+            const double x0 = xm[t];
+            int64_t e = t + 1;
+            while (e < T && e - t < p->K && (xm[e] - x0) / eps * wmax <= limit) ++e;
+            t = e;
+        }
+        ts.push_back((uint32_t)T);
+    }
+    const int nt = (int)ts.size() - 1;
+    p->nt = nt;
+    p->h_tile_of.resize(T);
+    std::vector<double> hxlb(nt), hxrb(nt);
+    std::vector<double> hspan(nt), hpos(T);
+    std::vector<int32_t> hcnt((size_t)nt * l), &href = p->h_reftile;
+    href.assign((size_t)nt * l, -1);
+    {
+        std::vector<int32_t> run(l, 0);
+        for (int b = 0; b < nt; ++b) {
+            hxlb[b] = xm[ts[b]];
+            hxrb[b] = xm[ts[b + 1] - 1];
+            hspan[b] = (hxrb[b] - hxlb[b]) / eps;
+            for (int k = 0; k < l; ++k) hcnt[(size_t)b * l + k] = run[k];
+            for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
+                hpos[t] = (xm[t] - hxlb[b]) / eps;
+                p->h_tile_of[t] = (uint32_t)b;
+                run[p->h_mid[t]] += 1;
+                href[(size_t)b * l + p->h_mid[t]] = b;
+            }
+        }
+        // tiles without points of marginal m use the nearest earlier tile
+        // that has some, else the nearest later one
+        for (int k = 0; k < l; ++k) {
+            int last = -1;
+            for (int b = 0; b < nt; ++b) {
+                int32_t &r = href[(size_t)b * l + k];
+                if (r == b) last = b;
+                else r = last;
+            }
+            int next = -1;
+            for (int b = nt - 1; b >= 0; --b) {
+                int32_t &r = href[(size_t)b * l + k];
+                if (r == b) next = b;
+                else if (r < 0) r = next;
+            }
+        }
+    }
+    p->h_beta.assign((size_t)nt * l, 0.0);
+    for (int b = 0; b < nt; ++b)
+        for (int k = 0; k < l; ++k) p->h_beta[(size_t)b * l + k] = -std::log((double)N[k]);
+
+    // ---- device allocation and upload -------------------------------------
+#define PA(ptr, n)                                          \
+    do {                                                    \
+        cudaError_t e_ = p->alloc(&ptr, (size_t)(n));       \
+        if (e_ != cudaSuccess) {                            \
+            delete p;                                       \
+            return fail(MMOT_ERR_OOM, "cudaMalloc %s", #ptr); \
+        }                                                   \
+    } while (0)
+    p->esz = fp64 ? 8 : 4;
+    {
+        unsigned char *q1 = nullptr, *q2 = nullptr;
+        PA(q1, (size_t)T * p->esz);
+        PA(q2, (size_t)T * p->esz);
+        p->pos = q1;
+        p->lphi = q2;
+    }
+    PA(p->mid, T);
+    PA(p->tstart, nt + 1);
+    PA(p->xlb, nt);
+    PA(p->xrb, nt);
+    PA(p->span, nt);
+    PA(p->cnt, (size_t)nt * l);
+    PA(p->reftile, (size_t)nt * l);
+    PA(p->beta, (size_t)nt * l);
+    int64_t maxN = 1;
+    for (int k = 0; k < l; ++k) {
+        PA(p->g[k], N[k]);
+        PA(p->lnmu[k], N[k]);
+        PA(p->mu[k], N[k]);
+        maxN = std::max(maxN, N[k]);
+    }
+    PA(p->agg, (size_t)nt * p->NS);
+    PA(p->inc, (size_t)nt * p->NS);
+    PA(p->bcarry, (size_t)nt * p->NS);
+    PA(p->partial, nt);
+    p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);
+    PA(p->flags, (size_t)nt * (p->NB + 1) + 1);
+    PA(p->err, 1);
+    PA(p->dsum, 8);
+    PA(p->scratch, maxN);
+#undef PA
+
+    auto up = [&](void *d, const void *h, size_t bytes) {
+        return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, p->st);
+    };
+    std::vector<unsigned char> hposb((size_t)T * p->esz), hl((size_t)T * p->esz, 0);
+    for (int64_t t = 0; t < T; ++t) {
+        if (fp64)
+            reinterpret_cast<double *>(hposb.data())[t] = hpos[t];
+        else
+            reinterpret_cast<float *>(hposb.data())[t] = (float)hpos[t];
+    }
+    cudaError_t ce = cudaSuccess;
+    ce = ce ? ce : up(p->pos, hposb.data(), hposb.size());
+    ce = ce ? ce : up(p->mid, p->h_mid.data(), T);
+    ce = ce ? ce : up(p->lphi, hl.data(), hl.size());
+    ce = ce ? ce : up(p->tstart, ts.data(), sizeof(uint32_t) * (nt + 1));
+    ce = ce ? ce : up(p->xlb, hxlb.data(), sizeof(double) * nt);
+    ce = ce ? ce : up(p->xrb, hxrb.data(), sizeof(double) * nt);
+    ce = ce ? ce : up(p->span, hspan.data(), sizeof(double) * nt);
+    ce = ce ? ce : up(p->cnt, hcnt.data(), sizeof(int32_t) * nt * l);
+    ce = ce ? ce : up(p->reftile, href.data(), sizeof(int32_t) * nt * l);
+    ce = ce ? ce : up(p->beta, p->h_beta.data(), sizeof(double) * nt * l);
+    std::vector<std::vector<double>> hg(l), hlm(l);
+    for (int k = 0; k < l && ce == cudaSuccess; ++k) {
+        hg[k].assign(N[k], -eps * std::log((double)N[k]));
+        hlm[k].resize(N[k]);
+        for (int64_t i = 0; i < N[k]; ++i) hlm[k][i] = hmu[k][i] > 0 ? std::log(hmu[k][i]) : -INFINITY;
+        ce = up(p->g[k], hg[k].data(), sizeof(double) * N[k]);
+        ce = ce ? ce : up(p->lnmu[k], hlm[k].data(), sizeof(double) * N[k]);
+        ce = ce ? ce : up(p->mu[k], hmu[k].data(), sizeof(double) * N[k]);
+    }
+    ce = ce ? ce : cudaMemsetAsync(p->err, 0, sizeof(int), p->st);
+    ce = ce ? ce : cudaStreamSynchronize(p->st);
+    if (ce != cudaSuccess) {
+        delete p;
+        return fail(MMOT_ERR_CUDA, "plan upload: %s", cudaGetErrorString(ce));
+    }
+    *out = p;
+    return MMOT_OK;
+}
+
+mmot_status mmot_marginal(mmot_plan p, int k, int plan_marginal, double *out)
+{
+    if (!p || !out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or out");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    int mode;
+    switch (plan_marginal) {
+    case 0: mode = MODE_OUT_M; break;
+    case 1: mode = MODE_OUT_PLAN; break;
+    case 2: mode = MODE_OUT_LNM; break;
+    default: return fail(MMOT_ERR_INVALID_ARG, "plan_marginal must be 0, 1 or 2");
+    }
+    const bool dev = is_device_ptr(out);
+    double *dst = dev ? out : p->scratch;
+    mmot_status s = enqueue_product(p, k, mode, dst);
+    if (s != MMOT_OK) return s;
+    if (!dev)
+        CUDA_TRY(cudaMemcpyAsync(out, p->scratch, sizeof(double) * p->N[k], cudaMemcpyDeviceToHost, p->st));
+    return check_device_error(p);
+}
+
+mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out)
+{
+    if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
+    if (n_iters < 0) return fail(MMOT_ERR_INVALID_ARG, "n_iters < 0");
+    if (n_iters > 0) {
+        if (p->use_graph) {
+            if (!p->graph) {
+                cudaGraph_t gr;
+                CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+                mmot_status s = enqueue_iteration(p);
+                cudaError_t e = cudaStreamEndCapture(p->st, &gr);
+                if (s != MMOT_OK) return s;
+                if (e != cudaSuccess) return fail(MMOT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+                e = cudaGraphInstantiate(&p->graph, gr, 0);
+                cudaGraphDestroy(gr);
+                if (e != cudaSuccess) {
+                    p->graph = nullptr;
+                    return fail(MMOT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+                }
+            }
+            for (int it = 0; it < n_iters; ++it) CUDA_TRY(cudaGraphLaunch(p->graph, p->st));
+        } else {
+            for (int it = 0; it < n_iters; ++it) {
+                mmot_status s = enqueue_iteration(p);
+                if (s != MMOT_OK) return s;
+            }
+        }
+    }
+    if (residual_out) {
+        mmot_status s = enqueue_residual(p, 0, p->l - 1);
+        if (s != MMOT_OK) return s;
+        s = read_scalar(p, p->dsum, residual_out);
+        if (s != MMOT_OK) return s;
+    }
+    return check_device_error(p);
+}
+
+mmot_status mmot_objective(mmot_plan p, mmot_result *out)
+{
+    if (!p || !out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or out");
+    memset(out, 0, sizeof(*out));
+    // marginals of the plan, one product per marginal
+    double P = 0.0, D = 0.0, Z = 0.0, res = 0.0;
+    for (int k = 0; k < p->l; ++k) {
+        std::vector<double> marg(p->N[k]), g(p->N[k]), m(p->N[k]);
+        mmot_status s = mmot_marginal(p, k, 1, marg.data());
+        if (s != MMOT_OK) return s;
+        CUDA_TRY(cudaMemcpy(g.data(), p->g[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(m.data(), p->mu[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
+        double z = 0.0;
+        for (int64_t i = 0; i < p->N[k]; ++i) {
+            z += marg[i];
+            res += std::fabs(marg[i] - m[i]);
+            if (std::isfinite(g[i])) {
+                P += g[i] * marg[i];
+                D += g[i] * m[i];
+            }
+        }
+        if (k == p->l - 1) Z = z;
+    }
+    out->iters = 0;
+    out->residual = res;
+    out->mass = Z;
+    out->primal = P;
+    out->dual = D + p->eps - p->eps * Z;
+    out->W = NAN;
+    return MMOT_OK;
+}
+
+mmot_status mmot_solve(mmot_plan p, double tol, int itr_max, mmot_result *out)
+{
+    if (!p || !out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or out");
+    if (itr_max < 0) return fail(MMOT_ERR_INVALID_ARG, "itr_max < 0");
+    int t = 0;
+    double res = INFINITY;
+    while (t < itr_max) {
+        const int n = (tol > 0.0) ? std::min(p->check_every, itr_max - t) : itr_max - t;
+        mmot_status s = mmot_sinkhorn_step(p, n, tol > 0.0 ? &res : nullptr);
+        if (s != MMOT_OK) return s;
+        t += n;
+        if (tol > 0.0 && res <= tol) break;
+    }
+    mmot_status s = mmot_objective(p, out);
+    if (s != MMOT_OK) return s;
+    if (tol <= 0.0 || t == 0) {
+        double r = 0.0;
+        s = enqueue_residual(p, 0, p->l - 1);
+        if (s != MMOT_OK) return s;
+        s = read_scalar(p, p->dsum, &r);
+        if (s != MMOT_OK) return s;
+        res = r;
+    }
+    out->iters = t;
+    out->residual = res;
+    s = check_device_error(p);
+    if (s != MMOT_OK) return s;
+    if (tol > 0.0 && res > tol) return fail(MMOT_ERR_NOT_CONVERGED, "residual %.3e > tol after %d iterations", res, t);
+    return MMOT_OK;
+}
+
+mmot_status mmot_get_potentials(mmot_plan p, int k, double *g_out)
+{
+    if (!p || !g_out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or output");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    CUDA_TRY(cudaMemcpyAsync(g_out, p->g[k], sizeof(double) * p->N[k], cudaMemcpyDefault, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    return MMOT_OK;
+}
+
+mmot_status mmot_set_potentials(mmot_plan p, int k, const double *g_in)
+{
+    if (!p || !g_in) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or input");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    std::vector<double> g(p->N[k]);
+    CUDA_TRY(cudaMemcpy(g.data(), g_in, sizeof(double) * p->N[k], cudaMemcpyDefault));
+    for (int64_t i = 0; i < p->N[k]; ++i)
+        if (std::isnan(g[i]) || g[i] == INFINITY)
+            return fail(MMOT_ERR_INVALID_ARG, "g[%lld] is NaN or +inf", (long long)i);
+    return upload_potential(p, k, g);
+}
+
+mmot_status mmot_set_option(mmot_plan p, int option, int64_t value)
+{
+    if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
+    switch (option) {
+    case MMOT_OPT_CHECK_EVERY:
+        if (value < 1) return fail(MMOT_ERR_INVALID_ARG, "check_every must be >= 1");
+        p->check_every = (int)value;
+        return MMOT_OK;
+    case MMOT_OPT_SPIN_LIMIT:
+        if (value < 1 || value > (1LL << 30)) return fail(MMOT_ERR_INVALID_ARG, "spin limit out of range");
+        p->spin_limit = (int)value;
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+        return MMOT_OK;
+    case MMOT_OPT_USE_GRAPH:
+        p->use_graph = value ? 1 : 0;
+        return MMOT_OK;
+    default: return fail(MMOT_ERR_INVALID_ARG, "unknown option %d", option);
+    }
+}
+
+mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
+{
+    if (!p || !info) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or info");
+    info->total_points = p->T;
+    info->tiles = p->nt;
+    info->tile_points = p->K;
+    info->threads_per_block = p->NT;
+    info->launches_per_iteration = 2 * p->l;
+    info->precision = p->prec;
+    return MMOT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Internal declarations shared by the host runtime and the sweep kernels.
+//
+// Terminology (arXiv 2405.19246, Sec. 3 and Sec. 4.2):
+//   merged order  all sum_k N_k support points sorted by (x, marginal, index);
+//                 the tie rule of the order classes D_p (Eq. D_p).
+//   target j      the marginal whose product M_j is evaluated; the other
+//                 marginals R = [l] \ {j} are mapped to bits 0..l-2.
+//   state S       a subset of R; F_S(z) sums over placements of one point of
+//                 each marginal of S left of z of prod phi * exp(-cost so far),
+//                 G_S(z) is the mirror image right of z.  Orderings that put
+//                 the same set left of z share one state: these are the
+//                 paper's class chains (Sec. 4.2) with shared prefixes.
+//   rate w_s      s(l-s): while s tuple points lie left of z, s(l-s) pairs
+//                 straddle z, so every state with |S| = s decays as
+//                 exp(-s(l-s) dx / eps) (the multiplier lambda^2 of
+//                 Algorithm 2 is the l = 3 case, w_1 = w_2 = 2).
+//   M_j(i)        sum_S F_S(x_i^-) G_{R\S}(x_i^+)   (Eq. Jk k margin).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define MMOT_MAXL 8
+
+namespace mmot {
+
+enum Mode : int {
+    MODE_UPDATE = 0,       // g_j <- eps (ln mu_j - ln M_j), refresh ln phi_j copy
+    MODE_OUT_M = 1,        // out[i] = M_j(i)
+    MODE_OUT_PLAN = 2,     // out[i] = phi_j(i) M_j(i)
+    MODE_OUT_LNM = 3,      // out[i] = ln M_j(i)
+    MODE_RESIDUAL = 4,     // partial[b] = sum over tile of |phi_j M_j - mu_j|
+};
+
+enum ErrBits : int {
+    ERR_TIMEOUT = 1,
+    ERR_NONFINITE = 2,
+    ERR_RANGE = 4,
+};
+
+// Everything a sweep kernel reads or writes; passed by value.
+struct SweepArgs {
+    int l;           // marginals
+    int j;           // target marginal
+    int nt;          // tiles
+    int mode;
+    int spin_limit;  // polls before a wait gives up
+    double eps;
+    // per tile
+    const uint32_t *tstart;   // [nt+1] first merged index of each tile
+    const double *xlb;        // [nt]   x of the first point of the tile
+    const double *xrb;        // [nt]   x of the last point of the tile
+    const double *span;       // [nt]   (xrb - xlb)/eps
+    const int32_t *cnt;       // [nt*l] points of marginal m before tile b
+    const int32_t *reftile;   // [nt*l] tile whose beta represents marginal m in tile b
+    double *beta;             // [nt*l] per-tile baseline of g_m/eps
+    // per merged point
+    // FP32 arrays for the FP32 path, FP64 arrays for the all-FP64 path
+    const void *pos;          // (x_t - xlb[b])/eps
+    const uint8_t *mid;       // marginal of the point
+    void *lphi;               // g_m(i)/eps - beta[b*l+m]
+    // inter-tile scan state, indexed by processing order v
+    double *agg;              // [nt*NS] ln of the tile's own contribution
+    double *inc;              // [nt*NS] ln of the inclusive prefix
+    int *flags;               // [nt*(NB+1)] 0 none, 1 aggregate, 2 inclusive, 3 failed
+    int *counter;             // dynamic tile counter
+    double *bcarry;           // [nt*NS] backward carries at each tile's right end
+    // target marginal
+    double *gj;               // [N_j] potentials (FP64)
+    const double *lnmuj;      // [N_j] ln mu_j (-inf for zero weights)
+    const double *muj;        // [N_j] mu_j
+    double *out;              // [N_j] output for the OUT modes
+    double *partial;          // [nt] per-tile residual sums
+    int *err;                 // error bits
+};
+
+// Host-side launchers (one per bit count NB = l-1, instantiated per precision).
+template <int NB, typename V>
+cudaError_t launch_bwd(const SweepArgs &a, cudaStream_t s);
+template <int NB, typename V>
+cudaError_t launch_fwd(const SweepArgs &a, cudaStream_t s);
+
+// Tile geometry chosen per (bits, precision): points per tile, threads,
+// maximum points of one marginal in a tile, and the tile span limit
+// max_s w_s * span (keeps in-tile exponents small).
+struct TileShape {
+    int K;
+    int NT;
+    int JCAP;
+    double span_limit;
+};
+TileShape tile_shape(int NB, bool fp64);
+
+}  // namespace mmot

@@ -1,0 +1,45 @@
+// Tile shapes per bit count NB (= l - 1) and precision.
+//
+// K = NT * C points per tile, one chunk of C consecutive points per thread.
+// The backward states of a tile are kept at its target points in shared memory
+// (NS x JCAP values), so K shrinks as the state count NS = 2^NB grows.
+// span_limit bounds max_s w_s * (x_last - x_first)/eps inside a tile, which
+// keeps every in-tile exponent small enough for the precision (FP32: the
+// exponent error is about 6e-8 * span_limit).
+#pragma once
+#include "mmot_internal.cuh"
+
+namespace mmot {
+
+template <int NB, typename V>
+struct Shape;
+
+#define MMOT_SHAPE(NB_, V_, NT_, C_)                 \
+    template <>                                      \
+    struct Shape<NB_, V_> {                          \
+        static constexpr int NT = NT_;               \
+        static constexpr int C = C_;                 \
+        static constexpr int K = NT_ * C_;           \
+        static constexpr int JCAP = NT_ * C_;        \
+    };
+
+MMOT_SHAPE(1, float, 256, 16)
+MMOT_SHAPE(2, float, 256, 16)
+MMOT_SHAPE(3, float, 256, 8)
+MMOT_SHAPE(4, float, 256, 4)
+MMOT_SHAPE(5, float, 128, 4)
+MMOT_SHAPE(6, float, 128, 2)
+MMOT_SHAPE(7, float, 128, 1)
+MMOT_SHAPE(1, double, 256, 8)
+MMOT_SHAPE(2, double, 256, 8)
+MMOT_SHAPE(3, double, 256, 4)
+MMOT_SHAPE(4, double, 256, 2)
+MMOT_SHAPE(5, double, 128, 2)
+MMOT_SHAPE(6, double, 128, 1)
+MMOT_SHAPE(7, double, 64, 1)
+#undef MMOT_SHAPE
+
+constexpr double kSpanLimitF32 = 24.0;
+constexpr double kSpanLimitF64 = 200.0;
+
+}  // namespace mmot

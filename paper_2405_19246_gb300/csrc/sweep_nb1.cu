@@ -1,0 +1,3 @@
+// Sweep kernels for l = 2 marginals (1 state bits).
+#include "sweep_inst.cuh"
+MMOT_INSTANTIATE(1)

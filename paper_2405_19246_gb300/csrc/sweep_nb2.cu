@@ -1,0 +1,3 @@
+// Sweep kernels for l = 3 marginals (2 state bits).
+#include "sweep_inst.cuh"
+MMOT_INSTANTIATE(2)

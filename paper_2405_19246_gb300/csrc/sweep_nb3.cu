@@ -1,0 +1,3 @@
+// Sweep kernels for l = 4 marginals (3 state bits).
+#include "sweep_inst.cuh"
+MMOT_INSTANTIATE(3)

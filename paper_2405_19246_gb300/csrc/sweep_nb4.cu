@@ -1,0 +1,3 @@
+// Sweep kernels for l = 5 marginals (4 state bits).
+#include "sweep_inst.cuh"
+MMOT_INSTANTIATE(4)

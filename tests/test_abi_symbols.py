@@ -1,0 +1,51 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function that include/mmot.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mmot.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mmot_[a-z_]+)\s*\(", src)))
+
+
+def test_header_lists_the_boundary():
+    names = _declared()
+    for required in ("mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve",
+                     "mmot_destroy", "mmot_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2405_19246_gb300 import _build, _native
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_native.EXPORTED) == set(_declared())
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch):
+    from paper_2405_19246_gb300 import _native
+    monkeypatch.setattr(_native, "_lib", None)
+    monkeypatch.setattr(_native, "LIB_PATH", os.path.join(ROOT, "does_not_exist.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _native.lib()
+
+
+def test_last_error_without_gpu():
+    from paper_2405_19246_gb300 import _build, _native
+    _build.build()
+    L = _native.lib()
+    # invalid arguments are rejected before any CUDA call
+    h = ctypes.c_void_p()
+    st = L.mmot_plan_create(1, None, None, None, 0.1, 1, 0, None, ctypes.byref(h))
+    assert st == 1
+    assert b"l = 1" in L.mmot_last_error()
+    L.mmot_destroy(None)
