@@ -120,12 +120,29 @@ mmot_status mmot_objective(mmot_plan p, mmot_result *out);
 mmot_status mmot_get_potentials(mmot_plan p, int k, double *g_out);
 mmot_status mmot_set_potentials(mmot_plan p, int k, const double *g_in);
 
+/* Reset every potential to the starting point phi_k = 1/N_k (Algorithm 1,
+ * line 1), i.e. g_k = -eps ln N_k, on the device (no host transfer). */
+mmot_status mmot_reset_potentials(mmot_plan p);
+
 /* Plan options (integers):
  *   MMOT_OPT_CHECK_EVERY   residual evaluation period in mmot_solve (default 10)
  *   MMOT_OPT_SPIN_LIMIT    inter-tile wait limit in polls (default ~1 s)
- *   MMOT_OPT_USE_GRAPH     capture the per-iteration launches in a CUDA graph (default 1) */
-enum { MMOT_OPT_CHECK_EVERY = 1, MMOT_OPT_SPIN_LIMIT = 2, MMOT_OPT_USE_GRAPH = 3 };
+ *   MMOT_OPT_USE_GRAPH     capture the per-iteration launches in a CUDA graph (default 1)
+ *   MMOT_OPT_PROFILE       1: bracket every kernel launch with CUDA events on the
+ *                          plan's stream and accumulate per-kernel times (graphs
+ *                          are not used while profiling); 0: off (default) */
+enum { MMOT_OPT_CHECK_EVERY = 1, MMOT_OPT_SPIN_LIMIT = 2, MMOT_OPT_USE_GRAPH = 3, MMOT_OPT_PROFILE = 4 };
 mmot_status mmot_set_option(mmot_plan p, int option, int64_t value);
+
+/* Per-kernel launch statistics collected while MMOT_OPT_PROFILE is on.
+ *   kernel 0: backward look-back scan (k_bwd), 1: forward look-back scan +
+ *   combine (k_fwd), 2: tile transfer operators (k_tileop), 3: carry scan over
+ *   tiles (k_carry), 4: tile products with known carries + combine (k_prod).
+ *   Plans with l <= 5 use kernels 2-4, larger l kernels 0-1.
+ * Returns the number of launches and their summed device time in ms (CUDA
+ * events on the plan's stream); synchronises the stream.  reset != 0 clears
+ * the statistics after reading. */
+mmot_status mmot_get_profile(mmot_plan p, int kernel, int64_t *launches, double *total_ms, int reset);
 
 /* Plan information: number of tiles, points per tile, total points, kernel
  * launches per Sinkhorn iteration. */
@@ -136,6 +153,7 @@ typedef struct {
     int threads_per_block;
     int launches_per_iteration;
     int precision;
+    int64_t kernel_launches;   /* library kernels launched on this plan so far */
 } mmot_plan_info;
 mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
 

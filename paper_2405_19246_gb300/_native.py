@@ -23,12 +23,13 @@ MMOT_FP32_SCAN_FP64_POT = 1
 MMOT_OPT_CHECK_EVERY = 1
 MMOT_OPT_SPIN_LIMIT = 2
 MMOT_OPT_USE_GRAPH = 3
+MMOT_OPT_PROFILE = 4
 
 # every symbol include/mmot.h declares
 EXPORTED = [
     "mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve", "mmot_objective",
-    "mmot_get_potentials", "mmot_set_potentials", "mmot_set_option", "mmot_get_info",
-    "mmot_destroy", "mmot_last_error",
+    "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
+    "mmot_get_profile", "mmot_get_info", "mmot_destroy", "mmot_last_error",
 ]
 
 
@@ -40,7 +41,8 @@ class MmotResult(ctypes.Structure):
 class MmotPlanInfo(ctypes.Structure):
     _fields_ = [("total_points", ctypes.c_int64), ("tiles", ctypes.c_int64),
                 ("tile_points", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-                ("launches_per_iteration", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("launches_per_iteration", ctypes.c_int), ("precision", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 class MmotError(RuntimeError):
@@ -70,7 +72,9 @@ def lib():
         L.mmot_objective.argtypes = [vp, P(MmotResult)]
         L.mmot_get_potentials.argtypes = [vp, i, vp]
         L.mmot_set_potentials.argtypes = [vp, i, vp]
+        L.mmot_reset_potentials.argtypes = [vp]
         L.mmot_set_option.argtypes = [vp, i, i64]
+        L.mmot_get_profile.argtypes = [vp, i, P(i64), P(d), i]
         L.mmot_get_info.argtypes = [vp, P(MmotPlanInfo)]
         L.mmot_destroy.argtypes = [vp]
         L.mmot_destroy.restype = None

@@ -132,6 +132,24 @@ class Plan:
             g = _host_f64(g)
             nat.check(nat.lib().mmot_set_potentials(self._h, k, g.ctypes.data))
 
+    def reset_potentials(self):
+        nat.check(nat.lib().mmot_reset_potentials(self._h))
+
+    def profile(self, on=True):
+        nat.check(nat.lib().mmot_set_option(self._h, nat.MMOT_OPT_PROFILE, 1 if on else 0))
+
+    def profile_stats(self, reset=True):
+        """{kernel name: (launches, total ms)} from the CUDA-event profile."""
+        out = {}
+        names = ((0, "k_bwd"), (1, "k_fwd"), (2, "k_tileop"), (3, "k_carry"), (4, "k_prod"))
+        for k, name in names:
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            nat.check(nat.lib().mmot_get_profile(self._h, k, ctypes.byref(n), ctypes.byref(ms),
+                                                 1 if (reset and k == 4) else 0))
+            out[name] = (n.value, ms.value)
+        return out
+
     def set_option(self, option, value):
         nat.check(nat.lib().mmot_set_option(self._h, int(option), int(value)))
 

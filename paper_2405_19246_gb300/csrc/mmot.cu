@@ -121,14 +121,21 @@ struct mmot_plan_s {
     void *lphi = nullptr;    // FP32 or FP64
     size_t esz = 4;
     uint32_t *tstart = nullptr;
-    double *xlb = nullptr, *xrb = nullptr;
+    double *ulb = nullptr, *urb = nullptr;   // tile ends in units of eps
     double *span = nullptr;
     int32_t *cnt = nullptr, *reftile = nullptr;
     double *beta = nullptr;
     double *g[MMOT_MAXL] = {nullptr};
     double *lnmu[MMOT_MAXL] = {nullptr};
     double *mu[MMOT_MAXL] = {nullptr};
-    double *agg = nullptr, *inc = nullptr, *bcarry = nullptr, *partial = nullptr;
+    // scaled floats: float2 (FP32 path) or double2 (FP64 path), sfsz bytes each
+    unsigned char *agg = nullptr, *inc = nullptr, *bcarry = nullptr;
+    unsigned char *fcarry = nullptr, *opF = nullptr, *opB = nullptr;
+    unsigned char *pdecF = nullptr, *pdecB = nullptr;
+    size_t sfsz = 8;
+    bool three_phase = false;  // tile operators + carry scan (l <= 5)
+    int ops_target = -1;       // target whose tile operators are current
+    double *partial = nullptr;
     int *flags = nullptr;   // flags followed by the tile counter
     size_t flags_bytes = 0;
     int *err = nullptr;
@@ -136,9 +143,20 @@ struct mmot_plan_s {
     double *scratch = nullptr;  // max N doubles
     cudaGraphExec_t graph = nullptr;
     std::vector<void *> allocs;
+    // profiling: pairs of events around each kernel launch
+    int profile = 0;
+    struct Rec { int kernel; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    int64_t prof_count[5] = {0, 0, 0, 0, 0};
+    int64_t launches = 0;   // kernels launched so far (graph replays included)
+    double prof_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 
     ~mmot_plan_s()
     {
+        for (auto &r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
         if (graph) cudaGraphExecDestroy(graph);
         for (void *p : allocs) cudaFree(p);
         if (own_stream && st) cudaStreamDestroy(st);
@@ -180,28 +198,59 @@ cudaError_t launch_sweep(int NB, const SweepArgs &a, bool fp64, cudaStream_t st,
     }
 }
 
+// kind: 2 tile operators, 3 carry scan, 4 product
 template <int NB>
-void shape_nb(bool fp64, int *K, int *NT)
+cudaError_t launch_ops_nb(const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
+{
+    if constexpr (NB <= kMaxOpBits) {
+        if (fp64) {
+            if (kind == 2) return launch_tileop<NB, double>(a, st);
+            if (kind == 3) return launch_carry<NB, double>(a, st);
+            return launch_prod<NB, double>(a, st);
+        }
+        if (kind == 2) return launch_tileop<NB, float>(a, st);
+        if (kind == 3) return launch_carry<NB, float>(a, st);
+        return launch_prod<NB, float>(a, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_ops(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
+{
+    switch (NB) {
+    case 1: return launch_ops_nb<1>(a, fp64, st, kind);
+    case 2: return launch_ops_nb<2>(a, fp64, st, kind);
+    case 3: return launch_ops_nb<3>(a, fp64, st, kind);
+    case 4: return launch_ops_nb<4>(a, fp64, st, kind);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NB>
+void shape_nb(bool fp64, int *K, int *NT, int *JCAP)
 {
     if (fp64) {
         *K = Shape<NB, double>::K;
         *NT = Shape<NB, double>::NT;
+        *JCAP = Shape<NB, double>::JCAP;
     } else {
         *K = Shape<NB, float>::K;
         *NT = Shape<NB, float>::NT;
+        *JCAP = Shape<NB, float>::JCAP;
     }
 }
 
-void shape_of(int NB, bool fp64, int *K, int *NT)
+void shape_of(int NB, bool fp64, int *K, int *NT, int *JCAP)
 {
     switch (NB) {
-    case 1: shape_nb<1>(fp64, K, NT); break;
-    case 2: shape_nb<2>(fp64, K, NT); break;
-    case 3: shape_nb<3>(fp64, K, NT); break;
-    case 4: shape_nb<4>(fp64, K, NT); break;
-    case 5: shape_nb<5>(fp64, K, NT); break;
-    case 6: shape_nb<6>(fp64, K, NT); break;
-    default: shape_nb<7>(fp64, K, NT); break;
+    case 1: shape_nb<1>(fp64, K, NT, JCAP); break;
+    case 2: shape_nb<2>(fp64, K, NT, JCAP); break;
+    case 3: shape_nb<3>(fp64, K, NT, JCAP); break;
+    case 4: shape_nb<4>(fp64, K, NT, JCAP); break;
+    case 5: shape_nb<5>(fp64, K, NT, JCAP); break;
+    case 6: shape_nb<6>(fp64, K, NT, JCAP); break;
+    default: shape_nb<7>(fp64, K, NT, JCAP); break;
     }
 }
 
@@ -215,9 +264,10 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.mode = mode;
     a.spin_limit = p->spin_limit;
     a.eps = p->eps;
+    a.inv_eps = 1.0 / p->eps;
     a.tstart = p->tstart;
-    a.xlb = p->xlb;
-    a.xrb = p->xrb;
+    a.ulb = p->ulb;
+    a.urb = p->urb;
     a.span = p->span;
     a.cnt = p->cnt;
     a.reftile = p->reftile;
@@ -230,6 +280,12 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.flags = p->flags;
     a.counter = p->flags + (size_t)p->nt * (p->NB + 1);
     a.bcarry = p->bcarry;
+    a.fcarry = p->fcarry;
+    a.opF = p->opF;
+    a.opB = p->opB;
+    a.pdecF = p->pdecF;
+    a.pdecB = p->pdecB;
+    a.jnext = -1;
     a.gj = p->g[j];
     a.lnmuj = p->lnmu[j];
     a.muj = p->mu[j];
@@ -239,26 +295,86 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     return a;
 }
 
-// One marginal product pass for target j: backward scan, then forward scan
-// with combine and epilogue.
-mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out)
+// kernel ids: 0 k_bwd, 1 k_fwd (look-back design); 2 k_tileop, 3 k_carry,
+// 4 k_prod (three-phase design)
+mmot_status timed_launch(mmot_plan p, int kernel, const SweepArgs &a, bool fp64)
 {
-    const SweepArgs a = make_args(p, j, mode, out);
-    const bool fp64 = (p->prec == MMOT_FP64);
-    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
-    CUDA_TRY(launch_sweep(p->NB, a, fp64, p->st, false));
-    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
-    CUDA_TRY(launch_sweep(p->NB, a, fp64, p->st, true));
+    p->launches += 1;
+    auto go = [&]() -> cudaError_t {
+        if (kernel <= 1) return launch_sweep(p->NB, a, fp64, p->st, kernel == 1);
+        return launch_ops(p->NB, a, fp64, p->st, kernel);
+    };
+    if (!p->profile) {
+        CUDA_TRY(go());
+        return MMOT_OK;
+    }
+    mmot_plan_s::Rec r;
+    r.kernel = kernel;
+    CUDA_TRY(cudaEventCreate(&r.a));
+    CUDA_TRY(cudaEventCreate(&r.b));
+    p->recs.push_back(r);
+    CUDA_TRY(cudaEventRecord(r.a, p->st));
+    CUDA_TRY(go());
+    CUDA_TRY(cudaEventRecord(r.b, p->st));
     return MMOT_OK;
 }
 
+// One marginal product for target j.  Look-back design: backward scan, then
+// forward scan with combine and epilogue.  Three-phase design: tile operators
+// (only if the current ones belong to another target), carry scan, then the
+// tile products; after an update the same launch computes the operators of
+// target jnext from the new potentials.
+mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext = -1)
+{
+    SweepArgs a = make_args(p, j, mode, out);
+    const bool fp64 = (p->prec == MMOT_FP64);
+    if (p->three_phase) {
+        mmot_status s;
+        if (p->ops_target != j) {
+            s = timed_launch(p, 2, a, fp64);
+            if (s != MMOT_OK) return s;
+            p->ops_target = j;
+        }
+        s = timed_launch(p, 3, a, fp64);
+        if (s != MMOT_OK) return s;
+        a.jnext = (mode == MODE_UPDATE) ? jnext : -1;
+        s = timed_launch(p, 4, a, fp64);
+        if (s != MMOT_OK) return s;
+        if (a.jnext >= 0) p->ops_target = a.jnext;
+        return MMOT_OK;
+    }
+    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
+    mmot_status s = timed_launch(p, 0, a, fp64);
+    if (s != MMOT_OK) return s;
+    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
+    return timed_launch(p, 1, a, fp64);
+}
+
+// g_k = -eps ln N_k, beta = -ln N_k, lphi = 0
+__global__ void k_reset(double *g, int64_t n, double v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] = v;
+}
+
+// One Gauss-Seidel iteration.  In the three-phase design it expects the tile
+// operators of target 0 to be current and leaves them current.
 mmot_status enqueue_iteration(mmot_plan p)
 {
     for (int j = 0; j < p->l; ++j) {
-        mmot_status s = enqueue_product(p, j, MODE_UPDATE, nullptr);
+        mmot_status s = enqueue_product(p, j, MODE_UPDATE, nullptr, (j + 1) % p->l);
         if (s != MMOT_OK) return s;
     }
     return MMOT_OK;
+}
+
+mmot_status ensure_ops(mmot_plan p, int j)
+{
+    if (!p->three_phase || p->ops_target == j) return MMOT_OK;
+    SweepArgs a = make_args(p, j, MODE_UPDATE, nullptr);
+    mmot_status s = timed_launch(p, 2, a, p->prec == MMOT_FP64);
+    if (s == MMOT_OK) p->ops_target = j;
+    return s;
 }
 
 mmot_status check_device_error(mmot_plan p)
@@ -284,6 +400,7 @@ mmot_status enqueue_residual(mmot_plan p, int k0, int k1)
         if (s != MMOT_OK) return s;
         k_sum_partials<<<1, 256, 0, p->st>>>(p->partial, p->nt, p->dsum, 1);
         CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
     }
     return MMOT_OK;
 }
@@ -333,6 +450,7 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
     CUDA_TRY(cudaMemcpyAsync(p->lphi, lp.data(), lp.size(), cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaMemcpyAsync(p->g[k], g.data(), sizeof(double) * p->N[k], cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaStreamSynchronize(p->st));
+    p->ops_target = -1;
     return MMOT_OK;
 }
 
@@ -403,7 +521,8 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     p->NB = l - 1;
     p->NS = 1 << p->NB;
     const bool fp64 = (prec == MMOT_FP64);
-    shape_of(p->NB, fp64, &p->K, &p->NT);
+    int jcap = 0;
+    shape_of(p->NB, fp64, &p->K, &p->NT, &jcap);
     if (cuda_stream) {
         p->st = (cudaStream_t)cuda_stream;
     } else {
@@ -434,7 +553,8 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
         }
     }
 
-    // ---- tiles: at most K points, span * max_s w_s <= limit --------------
+    // ---- tiles: at most K points, at most jcap points of one marginal,
+    //      span * max_s w_s <= limit ---------------------------------------
     double wmax = 0.0;
     for (int s = 0; s <= l; ++s) wmax = std::max(wmax, (double)s * (l - s));
     const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
@@ -442,11 +562,17 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     ts.clear();
     {
         int64_t t = 0;
+        std::vector<int> per(l, 0);
         while (t < T) {
             ts.push_back((uint32_t)t);
             const double x0 = xm[t];
+            std::fill(per.begin(), per.end(), 0);
+            per[p->h_mid[t]] = 1;
             int64_t e = t + 1;
-            while (e < T && e - t < p->K && (xm[e] - x0) / eps * wmax <= limit) ++e;
+            while (e < T && e - t < p->K && (xm[e] - x0) / eps * wmax <= limit && per[p->h_mid[e]] < jcap) {
+                per[p->h_mid[e]] += 1;
+                ++e;
+            }
             t = e;
         }
         ts.push_back((uint32_t)T);
@@ -512,8 +638,8 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     }
     PA(p->mid, T);
     PA(p->tstart, nt + 1);
-    PA(p->xlb, nt);
-    PA(p->xrb, nt);
+    PA(p->ulb, nt);
+    PA(p->urb, nt);
     PA(p->span, nt);
     PA(p->cnt, (size_t)nt * l);
     PA(p->reftile, (size_t)nt * l);
@@ -525,9 +651,18 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
         PA(p->mu[k], N[k]);
         maxN = std::max(maxN, N[k]);
     }
-    PA(p->agg, (size_t)nt * p->NS);
-    PA(p->inc, (size_t)nt * p->NS);
-    PA(p->bcarry, (size_t)nt * p->NS);
+    p->sfsz = fp64 ? 16 : 8;
+    PA(p->agg, (size_t)nt * p->NS * p->sfsz);
+    PA(p->inc, (size_t)nt * p->NS * p->sfsz);
+    PA(p->bcarry, (size_t)nt * p->NS * p->sfsz);
+    p->three_phase = (p->NB <= kMaxOpBits);
+    if (p->three_phase) {
+        PA(p->fcarry, (size_t)nt * p->NS * p->sfsz);
+        PA(p->opF, (size_t)nt * p->NB * p->NS * p->sfsz);
+        PA(p->opB, (size_t)nt * p->NB * p->NS * p->sfsz);
+        PA(p->pdecF, (size_t)nt * (p->NB + 1) * p->sfsz);
+        PA(p->pdecB, (size_t)nt * (p->NB + 1) * p->sfsz);
+    }
     PA(p->partial, nt);
     p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);
     PA(p->flags, (size_t)nt * (p->NB + 1) + 1);
@@ -551,8 +686,49 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     ce = ce ? ce : up(p->mid, p->h_mid.data(), T);
     ce = ce ? ce : up(p->lphi, hl.data(), hl.size());
     ce = ce ? ce : up(p->tstart, ts.data(), sizeof(uint32_t) * (nt + 1));
-    ce = ce ? ce : up(p->xlb, hxlb.data(), sizeof(double) * nt);
-    ce = ce ? ce : up(p->xrb, hxrb.data(), sizeof(double) * nt);
+    std::vector<double> hulb(nt), hurb(nt);
+    for (int b = 0; b < nt; ++b) {
+        hulb[b] = hxlb[b] / eps;
+        hurb[b] = hxrb[b] / eps;
+    }
+    ce = ce ? ce : up(p->ulb, hulb.data(), sizeof(double) * nt);
+    ce = ce ? ce : up(p->urb, hurb.data(), sizeof(double) * nt);
+    // exp(-w_s d) from each tile base to the next base in processing order, as
+    // scaled floats m * 2^k
+    std::vector<unsigned char> hdecF, hdecB;
+    if (p->three_phase) {
+        const int NB1 = p->NB + 1;
+        hdecF.assign((size_t)nt * NB1 * p->sfsz, 0);
+        hdecB.assign((size_t)nt * NB1 * p->sfsz, 0);
+        auto put = [&](std::vector<unsigned char> &dst, size_t idx, double lnv) {
+            const double y = lnv / std::log(2.0);
+            const double n = std::floor(y);
+            int e = 0;
+            const double m = std::frexp(std::exp2(y - n), &e);
+            const long long k = (long long)n + e;
+            if (fp64) {
+                double *q = reinterpret_cast<double *>(dst.data()) + 2 * idx;
+                q[0] = (y < -1.0e9) ? 0.0 : m;
+                q[1] = (y < -1.0e9) ? 0.0 : (double)k;
+            } else {
+                float *q = reinterpret_cast<float *>(dst.data()) + 2 * idx;
+                const int ki = (y < -1.0e9) ? 0 : (int)k;
+                q[0] = (y < -1.0e9) ? 0.0f : (float)m;
+                std::memcpy(&q[1], &ki, sizeof(int));
+            }
+        };
+        for (int b = 0; b < nt; ++b) {
+            const double dF = (b + 1 < nt) ? hulb[b + 1] - hulb[b] : 0.0;
+            const double dB = (b >= 1) ? hurb[b] - hurb[b - 1] : 0.0;
+            for (int sl = 0; sl < NB1; ++sl) {
+                const double ws = (double)sl * (double)(l - sl);
+                put(hdecF, (size_t)b * NB1 + sl, -ws * dF);
+                put(hdecB, (size_t)b * NB1 + sl, -ws * dB);
+            }
+        }
+        ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
+        ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());
+    }
     ce = ce ? ce : up(p->span, hspan.data(), sizeof(double) * nt);
     ce = ce ? ce : up(p->cnt, hcnt.data(), sizeof(int32_t) * nt * l);
     ce = ce ? ce : up(p->reftile, href.data(), sizeof(int32_t) * nt * l);
@@ -601,11 +777,15 @@ mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out)
     if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
     if (n_iters < 0) return fail(MMOT_ERR_INVALID_ARG, "n_iters < 0");
     if (n_iters > 0) {
-        if (p->use_graph) {
+        mmot_status s0 = ensure_ops(p, 0);
+        if (s0 != MMOT_OK) return s0;
+        if (p->use_graph && !p->profile) {
             if (!p->graph) {
                 cudaGraph_t gr;
                 CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+                const int64_t before = p->launches;
                 mmot_status s = enqueue_iteration(p);
+                p->launches = before;   // captured, not launched
                 cudaError_t e = cudaStreamEndCapture(p->st, &gr);
                 if (s != MMOT_OK) return s;
                 if (e != cudaSuccess) return fail(MMOT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -616,7 +796,10 @@ mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out)
                     return fail(MMOT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
                 }
             }
-            for (int it = 0; it < n_iters; ++it) CUDA_TRY(cudaGraphLaunch(p->graph, p->st));
+            for (int it = 0; it < n_iters; ++it) {
+                CUDA_TRY(cudaGraphLaunch(p->graph, p->st));
+                p->launches += 2 * p->l;
+            }
         } else {
             for (int it = 0; it < n_iters; ++it) {
                 mmot_status s = enqueue_iteration(p);
@@ -736,8 +919,54 @@ mmot_status mmot_set_option(mmot_plan p, int option, int64_t value)
     case MMOT_OPT_USE_GRAPH:
         p->use_graph = value ? 1 : 0;
         return MMOT_OK;
+    case MMOT_OPT_PROFILE:
+        p->profile = value ? 1 : 0;
+        return MMOT_OK;
     default: return fail(MMOT_ERR_INVALID_ARG, "unknown option %d", option);
     }
+}
+
+mmot_status mmot_reset_potentials(mmot_plan p)
+{
+    if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
+    const int l = p->l;
+    for (int k = 0; k < l; ++k) {
+        k_reset<<<64, 256, 0, p->st>>>(p->g[k], p->N[k], -p->eps * std::log((double)p->N[k]));
+        CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
+    }
+    for (int b = 0; b < p->nt; ++b)
+        for (int k = 0; k < l; ++k) p->h_beta[(size_t)b * l + k] = -std::log((double)p->N[k]);
+    CUDA_TRY(cudaMemcpyAsync(p->beta, p->h_beta.data(), sizeof(double) * p->h_beta.size(),
+                             cudaMemcpyHostToDevice, p->st));
+    CUDA_TRY(cudaMemsetAsync(p->lphi, 0, (size_t)p->T * p->esz, p->st));
+    p->ops_target = -1;
+    return MMOT_OK;
+}
+
+mmot_status mmot_get_profile(mmot_plan p, int kernel, int64_t *launches, double *total_ms, int reset)
+{
+    if (!p || !launches || !total_ms) return fail(MMOT_ERR_INVALID_ARG, "NULL argument");
+    if (kernel < 0 || kernel > 4) return fail(MMOT_ERR_INVALID_ARG, "kernel must be in 0..4");
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    for (auto &r : p->recs) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        p->prof_count[r.kernel] += 1;
+        p->prof_ms[r.kernel] += ms;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    p->recs.clear();
+    *launches = p->prof_count[kernel];
+    *total_ms = p->prof_ms[kernel];
+    if (reset) {
+        for (int q = 0; q < 5; ++q) {
+            p->prof_count[q] = 0;
+            p->prof_ms[q] = 0.0;
+        }
+    }
+    return MMOT_OK;
 }
 
 mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
@@ -747,8 +976,9 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
     info->tiles = p->nt;
     info->tile_points = p->K;
     info->threads_per_block = p->NT;
-    info->launches_per_iteration = 2 * p->l;
+    info->launches_per_iteration = 2 * p->l;   // both designs: two kernels per product
     info->precision = p->prec;
+    info->kernel_launches = p->launches;
     return MMOT_OK;
 }
 

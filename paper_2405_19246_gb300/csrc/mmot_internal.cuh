@@ -45,10 +45,11 @@ struct SweepArgs {
     int mode;
     int spin_limit;  // polls before a wait gives up
     double eps;
+    double inv_eps;
     // per tile
     const uint32_t *tstart;   // [nt+1] first merged index of each tile
-    const double *xlb;        // [nt]   x of the first point of the tile
-    const double *xrb;        // [nt]   x of the last point of the tile
+    const double *ulb;        // [nt]   x/eps of the first point of the tile
+    const double *urb;        // [nt]   x/eps of the last point of the tile
     const double *span;       // [nt]   (xrb - xlb)/eps
     const int32_t *cnt;       // [nt*l] points of marginal m before tile b
     const int32_t *reftile;   // [nt*l] tile whose beta represents marginal m in tile b
@@ -59,11 +60,23 @@ struct SweepArgs {
     const uint8_t *mid;       // marginal of the point
     void *lphi;               // g_m(i)/eps - beta[b*l+m]
     // inter-tile scan state, indexed by processing order v
-    double *agg;              // [nt*NS] ln of the tile's own contribution
-    double *inc;              // [nt*NS] ln of the inclusive prefix
+    // values are scaled floats (m, k) = m * 2^k, stored as float2 (FP32 path,
+    // k in the bits of .y) or double2 (FP64 path)
+    void *agg;                // [nt*NS] the tile's own contribution at its base
+    void *inc;                // [nt*NS] inclusive prefix at the tile's base
     int *flags;               // [nt*(NB+1)] 0 none, 1 aggregate, 2 inclusive, 3 failed
     int *counter;             // dynamic tile counter
-    double *bcarry;           // [nt*NS] backward carries at each tile's right end
+    void *bcarry;             // [nt*NS] backward carries at each tile's right end
+    void *fcarry;             // [nt*NS] forward carries at each tile's left end
+    // carry-free tile transfer operators (decay to the next tile base
+    // included): op[(b*NB + s)*NS + U], forward and backward
+    void *opF;
+    void *opB;
+    // exp(-w_s d) from each tile base to the next one in processing order,
+    // [nt*(NB+1)], forward and backward
+    const void *pdecF;
+    const void *pdecB;
+    int jnext;                // target of the operators computed after an update (-1: none)
     // target marginal
     double *gj;               // [N_j] potentials (FP64)
     const double *lnmuj;      // [N_j] ln mu_j (-inf for zero weights)
@@ -74,10 +87,20 @@ struct SweepArgs {
 };
 
 // Host-side launchers (one per bit count NB = l-1, instantiated per precision).
+// Look-back design (every l): k_bwd then k_fwd.
 template <int NB, typename V>
 cudaError_t launch_bwd(const SweepArgs &a, cudaStream_t s);
 template <int NB, typename V>
 cudaError_t launch_fwd(const SweepArgs &a, cudaStream_t s);
+// Three-phase design (l <= 5): tile operators, carry scan over tiles, tile
+// products with known carries (optionally followed by the operators of a.jnext).
+template <int NB, typename V>
+cudaError_t launch_tileop(const SweepArgs &a, cudaStream_t s);
+template <int NB, typename V>
+cudaError_t launch_carry(const SweepArgs &a, cudaStream_t s);
+template <int NB, typename V>
+cudaError_t launch_prod(const SweepArgs &a, cudaStream_t s);
+constexpr int kMaxOpBits = 4;
 
 // Tile geometry chosen per (bits, precision): points per tile, threads,
 // maximum points of one marginal in a tile, and the tile span limit

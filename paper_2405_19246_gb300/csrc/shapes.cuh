@@ -14,13 +14,15 @@ namespace mmot {
 template <int NB, typename V>
 struct Shape;
 
-#define MMOT_SHAPE(NB_, V_, NT_, C_)                 \
-    template <>                                      \
-    struct Shape<NB_, V_> {                          \
-        static constexpr int NT = NT_;               \
-        static constexpr int C = C_;                 \
-        static constexpr int K = NT_ * C_;           \
-        static constexpr int JCAP = NT_ * C_;        \
+// JCAP: at most this many points of one marginal in a tile (the tiling cuts a
+// tile early otherwise); half the tile for l >= 3.
+#define MMOT_SHAPE(NB_, V_, NT_, C_)                             \
+    template <>                                                  \
+    struct Shape<NB_, V_> {                                      \
+        static constexpr int NT = NT_;                           \
+        static constexpr int C = C_;                             \
+        static constexpr int K = NT_ * C_;                       \
+        static constexpr int JCAP = (NB_ >= 2) ? NT_ * C_ / 2 : NT_ * C_; \
     };
 
 MMOT_SHAPE(1, float, 256, 16)

@@ -35,6 +35,7 @@
 // at the target points, then applies the FP64 epilogue (potential update
 // g_j = eps (ln mu_j - ln M_j), or an output mode).
 #pragma once
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
@@ -59,13 +60,168 @@ template <>
 __device__ __forceinline__ float vexp<float>(float x) { return __expf(x); }
 template <>
 __device__ __forceinline__ double vexp<double>(double x) { return exp(x); }
+template <typename V>
+__device__ __forceinline__ V vlog(V x);
+template <>
+__device__ __forceinline__ float vlog<float>(float x) { return logf(x); }
+template <>
+__device__ __forceinline__ double vlog<double>(double x) { return log(x); }
 
-__device__ __forceinline__ double lae(double a, double b)
+// exp of an FP64 argument to the accuracy of V (FP32: exp2f of the
+// fractional part of x*log2(e), the integer part scales the exponent)
+template <typename V>
+__device__ __forceinline__ double exp_acc(double x);
+template <>
+__device__ __forceinline__ double exp_acc<double>(double x) { return exp(x); }
+template <>
+__device__ __forceinline__ double exp_acc<float>(double x)
 {
-    if (a == -INFINITY) return b;
-    if (b == -INFINITY) return a;
-    const double m = fmax(a, b);
-    return m + log1p(exp(fmin(a, b) - m));
+    if (!(x > -1.0e300)) return 0.0;
+    const double y = x * 1.4426950408889634074;
+    if (y > 1.0e4) return INFINITY;
+    if (y < -1.0e4) return 0.0;
+    const double n = floor(y);
+    return ldexp((double)exp2f((float)(y - n)), (int)n);
+}
+
+constexpr double kLog2e = 1.4426950408889634074;  // log2(e)
+constexpr double kLn2 = 0.69314718055994530942;    // ln(2)
+
+template <typename V>
+__device__ __forceinline__ V vexp2(V x);
+template <>
+__device__ __forceinline__ float vexp2<float>(float x) { return exp2f(x); }
+template <>
+__device__ __forceinline__ double vexp2<double>(double x) { return exp2(x); }
+template <typename V>
+__device__ __forceinline__ V vldexp(V x, int e);
+template <>
+__device__ __forceinline__ float vldexp<float>(float x, int e) { return ldexpf(x, e); }
+template <>
+__device__ __forceinline__ double vldexp<double>(double x, int e) { return ldexp(x, e); }
+template <typename V>
+__device__ __forceinline__ V vfrexp(V x, int *e);
+template <>
+__device__ __forceinline__ float vfrexp<float>(float x, int *e) { return frexpf(x, e); }
+template <>
+__device__ __forceinline__ double vfrexp<double>(double x, int *e) { return frexp(x, e); }
+
+// Scaled float: value = m * 2^k with m = 0 or 0.5 <= m < 1.  Carries between
+// tiles span far more than the FP32 (or FP64) exponent range; keeping the
+// binary exponent as an integer makes products with exp(x) for a large FP64 x
+// cost one exp2 of the fractional part of x*log2(e) and no FP64
+// transcendental.
+template <typename V>
+struct Sf {
+    V m;
+    int k;
+};
+
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_zero() { return Sf<V>{V(0), 0}; }
+
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_make(V x)
+{
+    Sf<V> r;
+    if (x == V(0)) {
+        r.m = V(0);
+        r.k = 0;
+    } else {
+        r.m = vfrexp<V>(x, &r.k);
+    }
+    return r;
+}
+
+// a * exp(x) for an FP64 exponent x (x = -inf gives 0)
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_scale_exp(Sf<V> a, double x)
+{
+    if (a.m == V(0) || !(x > -1.0e300)) return sf_zero<V>();
+    const double y = fmin(x * kLog2e, 1.0e9);
+    if (y < -1.0e9) return sf_zero<V>();
+    const double n = floor(y);
+    Sf<V> r = sf_make<V>(a.m * vexp2<V>((V)(y - n)));
+    r.k += a.k + (int)n;
+    return r;
+}
+
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_add(Sf<V> a, Sf<V> b)
+{
+    if (a.m == V(0)) return b;
+    if (b.m == V(0)) return a;
+    const int k = max(a.k, b.k);
+    Sf<V> r = sf_make<V>(vldexp<V>(a.m, a.k - k) + vldexp<V>(b.m, b.k - k));
+    r.k += k;
+    return r;
+}
+
+// value * 2^(-shift)
+template <typename V>
+__device__ __forceinline__ V sf_value(Sf<V> a, int shift)
+{
+    return (a.m == V(0)) ? V(0) : vldexp<V>(a.m, a.k - shift);
+}
+
+// sum over the 32 lanes; every lane receives lane 0's result
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_warp_sum(Sf<V> a)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    int kmax = (a.m == V(0)) ? INT_MIN : a.k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+    if (kmax == INT_MIN) return sf_zero<V>();
+    V m = (a.m == V(0)) ? V(0) : vldexp<V>(a.m, a.k - kmax);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = __shfl_down_sync(FULL, m, o);
+        if ((threadIdx.x & 31) + o < 32) m += y;
+    }
+    m = __shfl_sync(FULL, m, 0);
+    Sf<V> r = sf_make<V>(m);
+    r.k += kmax;
+    return r;
+}
+
+// storage form of a scaled float
+template <typename V>
+struct SfSt;
+template <>
+struct SfSt<float> {
+    using T = float2;
+};
+template <>
+struct SfSt<double> {
+    using T = double2;
+};
+template <typename V>
+using SfT = typename SfSt<V>::T;
+
+__device__ __forceinline__ float2 sf_store(Sf<float> a) { return make_float2(a.m, __int_as_float(a.k)); }
+__device__ __forceinline__ double2 sf_store(Sf<double> a) { return make_double2(a.m, (double)a.k); }
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_load(SfT<V> d);
+template <>
+__device__ __forceinline__ Sf<float> sf_load<float>(float2 d) { return Sf<float>{d.x, __float_as_int(d.y)}; }
+template <>
+__device__ __forceinline__ Sf<double> sf_load<double>(double2 d) { return Sf<double>{d.x, (int)d.y}; }
+template <typename V>
+__device__ __forceinline__ SfT<V> *sfp(void *p) { return static_cast<SfT<V> *>(p); }
+template <typename V>
+__device__ __forceinline__ const SfT<V> *sfp(const void *p) { return static_cast<const SfT<V> *>(p); }
+template <typename V>
+__device__ __forceinline__ SfT<V> sf_one_st() { return sf_store(Sf<V>{V(0.5), 1}); }
+
+// a * b
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_mul(Sf<V> a, Sf<V> b)
+{
+    if (a.m == V(0) || b.m == V(0)) return sf_zero<V>();
+    Sf<V> r = sf_make<V>(a.m * b.m);
+    r.k += a.k + b.k;
+    return r;
 }
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -109,7 +265,9 @@ struct SweepSmem {
     static constexpr int NS = 1 << NB;
     static constexpr int K = NT * C;
     static constexpr int NW = NT / 32;
-    double E[NS];          // FP64 log carry of each state at the tile base
+    Sf<V> E[NS];           // carry of each state at the tile base (absolute)
+    Sf<V> Eh[NS];          // the same times exp(-sum_{m in S} beta_m)
+    Sf<V> Gs[NB + 2];      // exp(gamma_s) of the current pass
     double gam[NB + 1];    // level scales of the current pass
     double gamG[NB + 1];   // level scales of the backward pass (k_fwd)
     double beta[NB];       // baselines of the marginals mapped to bits
@@ -126,7 +284,11 @@ struct SweepSmem {
     V lphi[K];
     int16_t slot[K];
     uint8_t mid[K];
-    V G[WITH_G ? NS * JCAP : 1];  // backward states at target points
+    // backward states at target points; also the scratch of the tile-operator
+    // composition (NB x NS x NT values)
+    static constexpr int OPSZ = (NB <= kMaxOpBits) ? NB * NS * (NT / 32) : 0;
+    static constexpr int GSZ = (NS * JCAP > OPSZ) ? NS * JCAP : OPSZ;
+    V G[WITH_G ? GSZ : 1];
 };
 
 // Per-thread engine: a contiguous chunk of C points of the tile, in the
@@ -151,6 +313,12 @@ struct Engine {
 
     // rate w_s = s(l - s) with l = NB + 1
     __device__ static constexpr V rate(int s) { return (V)(s * (NB + 1 - s)); }
+    // provisional level shift of level s in a tile of the given span
+    __device__ static V dshift(int s, V span)
+    {
+        const V as = rate(s) - rate(s - 1);
+        return (as > V(0)) ? as * span : V(0);
+    }
 
     __device__ void setup(Sm &sm, int n, V span, bool fwd, int j)
     {
@@ -173,33 +341,21 @@ struct Engine {
                 bit[c] = (m == j) ? -1 : (m < j ? m : m - 1);
                 pp[c] = fwd ? sm.pos[id] : span - sm.pos[id];
                 lph[c] = sm.lphi[id];
-                if (bit[c] >= 0) {
-#pragma unroll
-                    for (int s = 1; s <= NB; ++s)
-                        dl[s - 1] = fmax(dl[s - 1], lph[c] + (rate(s) - rate(s - 1)) * pp[c]);
-                }
+
             }
         }
-        // block max of the injection exponents per level
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
-            V x = dl[s];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(FULL, x, o));
-            if (lane == 0) sm.fred[w][s] = x;
-        }
-        __syncthreads();
-        if (tid < NB) {
-            V x = V(-INFINITY);
-            for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][tid]);
-            sm.D[tid] = (x == V(-INFINITY)) ? V(0) : x;
-        }
-        __syncthreads();
+        // Level shift D_s = max(0, a_s span): ln phi <= 0 inside a tile (the
+        // baselines are the per-tile maxima) and 0 <= p <= span, so every
+        // injection factor exp(ln phi + a_s p - D_s) is at most 1.
+        (void)dl;
+        (void)lane;
+        (void)w;
+        if (tid < NB) sm.D[tid] = Engine::dshift(tid + 1, span);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
 #pragma unroll
             for (int s = 1; s <= NB; ++s) {
-                const V ex = lph[c] + (rate(s) - rate(s - 1)) * pp[c] - sm.D[s - 1];
+                const V ex = lph[c] + (rate(s) - rate(s - 1)) * pp[c] - dshift(s, span);
                 fac[c][s - 1] = (bit[c] >= 0) ? vexp<V>(ex) : V(0);
             }
         }
@@ -304,23 +460,23 @@ struct Engine {
 
     // Look-back for level s (warp 0): publish the tile aggregate, combine the
     // predecessors' aggregates / inclusive prefixes into sm.E, publish the
-    // inclusive prefix.
+    // inclusive prefix.  The 32 lanes inspect a window of 32 predecessors at
+    // once; the window moves back until it holds an inclusive prefix.
     template <int s>
     __device__ void lookback(Sm &sm, const SweepArgs &a, int v, int b, bool fwd)
     {
         const int lane = threadIdx.x & 31;
         constexpr int NQ = (NS + 31) / 32;
         const double ws = (double)s * (double)(NB + 1 - s);
-        double aggv[NQ], acc[NQ];
+        Sf<V> own[NQ], acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int S = lane + 32 * q;
-            aggv[q] = -INFINITY;
-            acc[q] = -INFINITY;
+            own[q] = sf_zero<V>();
+            acc[q] = sf_zero<V>();
             if (S < NS && popc_c(S) == s) {
-                const double A = (double)sm.tot[S];
-                aggv[q] = (A > 0.0) ? log(A) + sum_beta(sm, S) + sm.gam[s] : -INFINITY;
-                a.agg[(size_t)v * NS + S] = aggv[q];
+                own[q] = sf_scale_exp(sf_make<V>(sm.tot[S]), sum_beta(sm, S) + sm.gam[s]);
+                sfp<V>(a.agg)[(size_t)v * NS + S] = sf_store(own[q]);
             }
         }
         int *myflag = a.flags + (size_t)v * (NB + 1) + s;
@@ -328,32 +484,75 @@ struct Engine {
         __syncwarp();
         if (lane == 0) st_release(myflag, 1);
         bool fail = false;
-        const double xb = fwd ? a.xlb[b] : a.xrb[b];
-        int p = v - 1;
-        while (p >= 0) {
-            const int f = wait_flag(a.flags + (size_t)p * (NB + 1) + s, a.err, a.spin_limit);
-            if (f < 0 || f == 3) {
+        const double ub = fwd ? a.ulb[b] : a.urb[b];
+        // every lane accumulates the terms of the predecessors it inspects;
+        // one warp reduction per state at the end
+        constexpr int NL = NS;   // per-state lane-local sums (only level s used)
+        Sf<V> part[NL];
+#pragma unroll
+        for (int S = 0; S < NL; ++S) part[S] = sf_zero<V>();
+        int base = v - 1;
+        while (base >= 0) {
+            const int p = base - lane;
+            int f = (p >= 0) ? ld_acquire(a.flags + (size_t)p * (NB + 1) + s) : 2;
+            unsigned incl;
+            int it = 0;
+            while (true) {
+                incl = __ballot_sync(FULL, f >= 2);
+                const int first = incl ? (__ffs(incl) - 1) : 31;
+                const bool mine = lane <= first;
+                if (!__ballot_sync(FULL, mine && f == 0)) break;
+                if (++it > a.spin_limit || ((it & 63) == 0 && *(volatile const int *)a.err != 0)) {
+                    fail = true;
+                    break;
+                }
+                __nanosleep(32);
+                if (mine && f == 0) f = ld_acquire(a.flags + (size_t)p * (NB + 1) + s);
+            }
+            if (fail) break;
+            const int first = incl ? (__ffs(incl) - 1) : 31;
+            if (__ballot_sync(FULL, lane <= first && f == 3)) {
                 fail = true;
                 break;
             }
-            const int bp = fwd ? p : a.nt - 1 - p;
-            const double d = (fwd ? (xb - a.xlb[bp]) : (a.xrb[bp] - xb)) / a.eps;
-            const double *src = (f == 2) ? a.inc : a.agg;
+            if (lane <= first && p >= 0) {
+                const int bp = fwd ? p : a.nt - 1 - p;
+                const double d = fwd ? (ub - a.ulb[bp]) : (a.urb[bp] - ub);
+                // decay exp(-w_s d) as (fraction, integer) of a power of two
+                const double y = -ws * d * kLog2e;
+                const double n = floor(y);
+                const V dm = vexp2<V>((V)(y - n));
+                const int dk = (y < -1.0e9) ? INT_MIN / 2 : (int)n;
+                const SfT<V> *src = sfp<V>((f == 2) ? a.inc : a.agg);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int S = lane + 32 * q;
-                if (S < NS && popc_c(S) == s)
-                    acc[q] = lae(acc[q], __ldcg(src + (size_t)p * NS + S) - ws * d);
+                for (int S = 0; S < NS; ++S) {
+                    if (popc_c(S) == s) {
+                        const Sf<V> raw = sf_load<V>(__ldcg(src + (size_t)p * NS + S));
+                        if (raw.m != V(0) && dk > INT_MIN / 2) {
+                            Sf<V> t = sf_make<V>(raw.m * dm);
+                            t.k += raw.k + dk;
+                            part[S] = sf_add(part[S], t);
+                        }
+                    }
+                }
             }
-            if (f == 2) break;
-            --p;
+            if (incl) break;
+            base -= 32;
+        }
+#pragma unroll
+        for (int S = 0; S < NS; ++S) {
+            if (popc_c(S) == s) {
+                const Sf<V> t = sf_warp_sum(part[S]);
+                if (lane == (S & 31)) acc[S >> 5] = t;
+            }
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int S = lane + 32 * q;
             if (S < NS && popc_c(S) == s) {
                 sm.E[S] = acc[q];
-                a.inc[(size_t)v * NS + S] = lae(acc[q], aggv[q]);
+                sm.Eh[S] = sf_scale_exp(acc[q], -sum_beta(sm, S));
+                sfp<V>(a.inc)[(size_t)v * NS + S] = sf_store(sf_add(acc[q], own[q]));
             }
         }
         __threadfence();
@@ -365,37 +564,44 @@ struct Engine {
     }
 
     // Choose the final scale of level s from the tile-end values and turn the
-    // tile carry into f-representation (warp 0).
+    // tile carry into f-representation (warp 0).  Relative to exp(sum beta_S)
+    // the tile-end value is R_S = Eh_S + A_S exp(gamma_s); the new scale is
+    // 2^kmax with kmax the largest binary exponent of the R_S, so every
+    // level-s value becomes at most 1.  FP32 (or FP64) and integer work only.
     template <int s>
     __device__ void normalise(Sm &sm)
     {
         const int lane = threadIdx.x & 31;
         constexpr int NQ = (NS + 31) / 32;
-        const double gs = sm.gam[s];
-        double L[NQ];
-        double gmax = -INFINITY;
+        const Sf<V> G = sm.Gs[s];
+        int kmax = INT_MIN;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int S = lane + 32 * q;
-            L[q] = -INFINITY;
             if (S < NS && popc_c(S) == s) {
-                const double A = (double)sm.tot[S];
-                L[q] = lae(sm.E[S] - sum_beta(sm, S), A > 0.0 ? log(A) + gs : -INFINITY);
-                gmax = fmax(gmax, L[q]);
+                const Sf<V> R = sf_add(sm.Eh[S], sf_mul(sf_make<V>(sm.tot[S]), G));
+                if (R.m != V(0)) kmax = max(kmax, R.k);
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(FULL, gmax, o));
-        const double gnew = (gmax == -INFINITY) ? gs : gmax;
+        for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+        const bool none = (kmax == INT_MIN);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int S = lane + 32 * q;
-            if (S < NS && popc_c(S) == s) sm.tc[S] = (V)exp(sm.E[S] - sum_beta(sm, S) - gnew);
+            if (S < NS && popc_c(S) == s) sm.tc[S] = none ? V(0) : sf_value(sm.Eh[S], kmax);
         }
         if (lane == 0) {
-            sm.rho = (V)exp(gs - gnew);
+            sm.rho = none ? V(1) : sf_value(G, kmax);
+            const double gnew = none ? sm.gam[s] : (double)kmax * kLn2;
+            const Sf<V> Gn = none ? G : Sf<V>{V(0.5), kmax + 1};
             sm.gam[s] = gnew;
-            if (s < NB) sm.gam[s + 1] = gnew + (double)sm.D[s];
+            sm.Gs[s] = Gn;
+            if (s < NB) {
+                const V Dn = sm.D[s];
+                sm.gam[s + 1] = gnew + (double)Dn;
+                sm.Gs[s + 1] = sf_mul(Gn, sf_make<V>(vexp<V>(Dn)));
+            }
         }
     }
 
@@ -422,12 +628,85 @@ struct Engine {
         __syncthreads();
     }
 
+    // ---- carry-free transfer operator of the chunk ------------------------
+    // op[s][U] (U non-empty, s + |U| <= NB): weight with which a state of
+    // level s at the chunk start reaches the state with the marginals U added
+    // at the chunk end, in the cumulative frame and f-representation of the
+    // tile.  op[0][U] is the chunk's own contribution (from the empty state).
+    // These are the paper's per-class nested sums (Sec. 4.2, J^{(l)} recursion)
+    // grouped by starting level, so a tile can be summarised without its carry.
+    __device__ static constexpr bool op_valid(int s, int U) { return U != 0 && s < NB && s + popc_c(U) <= NB; }
+
+    template <int KB>
+    __device__ __forceinline__ void op_inject(V (&op)[NB][NS], int c)
+    {
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+#pragma unroll
+            for (int U = 1; U < NS; ++U) {
+                if (((U >> KB) & 1) && s + popc_c(U) <= NB) {
+                    const int W = U ^ (1 << KB);
+                    const V prev = (W == 0) ? V(1) : op[s][W];
+                    op[s][U] = fma(fac[c][s + popc_c(U) - 1], prev, op[s][U]);
+                }
+            }
+        }
+    }
+
+    template <int KB = 0>
+    __device__ __forceinline__ void op_dispatch(V (&op)[NB][NS], int k, int c)
+    {
+        if constexpr (KB < NB) {
+            if (k == KB)
+                op_inject<KB>(op, c);
+            else
+                op_dispatch<KB + 1>(op, k, c);
+        }
+    }
+
+    __device__ void op_walk(V (&op)[NB][NS])
+    {
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int U = 0; U < NS; ++U) op[s][U] = V(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int k = bit[c];
+            if (k >= 0) op_dispatch(op, k, c);
+        }
+    }
+
+    // R = X then Y (both in the same frame and representation)
+    __device__ static void op_compose(const V (&X)[NB][NS], const V (&Y)[NB][NS], V (&R)[NB][NS])
+    {
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+#pragma unroll
+            for (int U = 1; U < NS; ++U) {
+                if (s + popc_c(U) <= NB) {
+                    V r = X[s][U] + Y[s][U];
+#pragma unroll
+                    for (int Vv = 1; Vv < NS; ++Vv) {
+                        if ((Vv & ~U) == 0 && Vv != U) r = fma(X[s][Vv], Y[s + popc_c(Vv)][U ^ Vv], r);
+                    }
+                    R[s][U] = r;
+                } else {
+                    R[s][U] = V(0);
+                }
+            }
+            R[s][0] = V(0);
+        }
+    }
+
     template <bool MAIN>
     __device__ void all_levels(Sm &sm, const SweepArgs &a, int v, int b, bool fwd)
     {
         if (threadIdx.x == 0) {
             sm.gam[0] = 0.0;
+            sm.Gs[0] = Sf<V>{V(0.5), 1};
             sm.gam[1] = (double)sm.D[0];
+            sm.Gs[1] = sf_make<V>(vexp<V>(sm.D[0]));
         }
         __syncthreads();
         static_for<1, NB + 1>([&](auto sc) {
@@ -437,28 +716,35 @@ struct Engine {
     }
 };
 
+// baselines of the marginals mapped to bits for target j
+template <int NB, typename V, int NT, int C, int JCAP, bool WITH_G>
+__device__ void load_betas(SweepSmem<NB, V, NT, C, JCAP, WITH_G> &sm, const SweepArgs &a, int b, int j)
+{
+    if (threadIdx.x < NB) {
+        const int k = threadIdx.x;
+        const int m = (k < j) ? k : k + 1;
+        const int rt = __ldg(a.reftile + (size_t)b * a.l + m);
+        sm.beta[k] = *(volatile const double *)(a.beta + (size_t)rt * a.l + m);
+    }
+}
+
 template <int NB, typename V, int NT, int C, int JCAP, bool WITH_G>
 __device__ void load_tile(SweepSmem<NB, V, NT, C, JCAP, WITH_G> &sm, const SweepArgs &a, int b,
-                          int n, uint32_t t0)
+                          int n, uint32_t t0, int j)
 {
     const V *pos = static_cast<const V *>(a.pos);
     const V *lphi = static_cast<const V *>(a.lphi);
     for (int i = threadIdx.x; i < n; i += NT) {
         sm.pos[i] = __ldg(pos + t0 + i);
-        sm.lphi[i] = __ldg(lphi + t0 + i);
+        sm.lphi[i] = lphi[t0 + i];
         sm.mid[i] = __ldg(a.mid + t0 + i);
     }
-    if (threadIdx.x < NB) {
-        const int k = threadIdx.x;
-        const int m = (k < a.j) ? k : k + 1;
-        const int rt = __ldg(a.reftile + (size_t)b * a.l + m);
-        sm.beta[k] = a.beta[(size_t)rt * a.l + m];
-    }
+    load_betas(sm, a, b, j);
     __syncthreads();
 }
 
 template <int NB, typename V, int NT, int C, int JCAP>
-__global__ void __launch_bounds__(NT) k_bwd(SweepArgs a)
+__global__ void __launch_bounds__(NT, 3) k_bwd(SweepArgs a)
 {
     using Sm = SweepSmem<NB, V, NT, C, JCAP, false>;
     using En = Engine<NB, V, NT, C, JCAP, false>;
@@ -473,35 +759,30 @@ __global__ void __launch_bounds__(NT) k_bwd(SweepArgs a)
     const int b = a.nt - 1 - v;
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
-    load_tile<NB, V, NT, C, JCAP, false>(sm, a, b, n, t0);
+    load_tile<NB, V, NT, C, JCAP, false>(sm, a, b, n, t0, a.j);
     En e;
     e.setup(sm, n, (V)a.span[b], false, a.j);
     e.template all_levels<true>(sm, a, v, b, false);
-    for (int S = threadIdx.x; S < NS; S += NT) a.bcarry[(size_t)b * NS + S] = (S == 0) ? 0.0 : sm.E[S];
+    for (int S = threadIdx.x; S < NS; S += NT)
+        sfp<V>(a.bcarry)[(size_t)b * NS + S] = (S == 0) ? sf_one_st<V>() : sf_store(sm.E[S]);
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
-__global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
+// One tile of a marginal product: backward states from the stored carry,
+// forward states (look-back when LOOKBACK, else from the stored forward carry),
+// combine at the target points and the FP64 epilogue.
+template <int NB, typename V, int NT, int C, int JCAP, bool LOOKBACK>
+__device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const SweepArgs &a, int v, int b)
 {
-    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
     using En = Engine<NB, V, NT, C, JCAP, true>;
     constexpr int NS = 1 << NB;
     constexpr int FULLS = NS - 1;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NW = NT / 32;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Sm &sm = *reinterpret_cast<Sm *>(smraw);
-    __shared__ int s_v;
-    if (threadIdx.x == 0) s_v = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int v = s_v;
-    if (v >= a.nt) return;
-    const int b = v;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
     const V span = (V)a.span[b];
-    load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0);
+    load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
 
     // ranks of the target points (forward order)
     {
@@ -544,7 +825,10 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
     En e;
     // ---- backward states inside the tile from the stored carry -------------
     e.setup(sm, n, span, false, a.j);
-    for (int S = tid; S < NS; S += NT) sm.E[S] = (S == 0) ? 0.0 : a.bcarry[(size_t)b * NS + S];
+    for (int S = tid; S < NS; S += NT) {
+        sm.E[S] = sf_load<V>(sfp<V>(a.bcarry)[(size_t)b * NS + S]);
+        sm.Eh[S] = sf_scale_exp(sm.E[S], -En::sum_beta(sm, S));
+    }
     __syncthreads();
     e.template all_levels<false>(sm, a, v, b, false);
     e.template walk<NB>([&](int c) {
@@ -557,9 +841,18 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
     if (tid <= NB) sm.gamG[tid] = sm.gam[tid];
     __syncthreads();
 
-    // ---- forward scan with look-back, then combine ---------------------------
+    // ---- forward states (look-back or stored carry), then combine ----------
     e.setup(sm, n, span, true, a.j);
-    e.template all_levels<true>(sm, a, v, b, true);
+    if constexpr (LOOKBACK) {
+        e.template all_levels<true>(sm, a, v, b, true);
+    } else {
+        for (int S = tid; S < NS; S += NT) {
+            sm.E[S] = sf_load<V>(sfp<V>(a.fcarry)[(size_t)b * NS + S]);
+            sm.Eh[S] = sf_scale_exp(sm.E[S], -En::sum_beta(sm, S));
+        }
+        __syncthreads();
+        e.template all_levels<false>(sm, a, v, b, true);
+    }
 
     // per-tile constants of the combine
     __shared__ double s_base;
@@ -577,9 +870,10 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
         }
     }
     __syncthreads();
-    double lnM[C];
+    // ln M = base + xM with the per-tile FP64 base and a small in-tile part
+    V xM[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) lnM[c] = 0.0;
+    for (int c = 0; c < C; ++c) xM[c] = V(0);
     const double base = s_base;
     e.template walk<NB>([&](int c) {
         const int sl = sm.slot[e.idx[c]];
@@ -606,39 +900,40 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
 #pragma unroll
         for (int s = 0; s <= NB; ++s)
             if (X[s] > V(0)) sum += vexp<V>(ev[s] - emax) * X[s];
-        lnM[c] = (sum > V(0)) ? base + (double)emax + log((double)sum) : -INFINITY;
+        xM[c] = (sum > V(0)) ? emax + vlog<V>(sum) : V(-INFINITY);
     });
 
     // ---- FP64 epilogue ------------------------------------------------------
     const int32_t off = a.cnt[(size_t)b * a.l + a.j];
     if (a.mode == MODE_UPDATE) {
-        double gv[C];
-        double gmax = -INFINITY;
+        // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base) - xM   (FP64)
+        double gq[C];
+        V qmax = V(-INFINITY);   // new baseline: the tile maximum of g_j/eps
         bool bad = false;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            gv[c] = -INFINITY;
+            gq[c] = -INFINITY;
             if (e.bit[c] == -1) {
                 const int i = off + sm.slot[e.idx[c]];
                 const double lm = a.lnmuj[i];
                 if (lm > -INFINITY) {
-                    gv[c] = a.eps * (lm - lnM[c]);
-                    if (!isfinite(gv[c])) bad = true;
-                    gmax = fmax(gmax, gv[c] / a.eps);
+                    gq[c] = (lm - base) - (double)xM[c];
+                    if (!isfinite(gq[c])) bad = true;
+                    qmax = fmax(qmax, (V)gq[c]);
                 }
             }
         }
         if (bad) atomicOr(a.err, ERR_NONFINITE);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(FULL, gmax, o));
-        if (lane == 0) sm.dred[w] = gmax;
+        for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
+        if (lane == 0) sm.fred[w][0] = qmax;
         __syncthreads();
         if (tid == 0) {
-            double x = -INFINITY;
-            for (int q = 0; q < NW; ++q) x = fmax(x, sm.dred[q]);
-            if (!isfinite(x)) x = 0.0;
-            sm.dred[0] = x;
-            if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = x;
+            V x = V(-INFINITY);
+            for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][0]);
+            const double bx = isfinite((double)x) ? (double)x : 0.0;
+            sm.dred[0] = bx;
+            if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = bx;
         }
         __syncthreads();
         const double bnew = sm.dred[0];
@@ -646,8 +941,10 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
         for (int c = 0; c < C; ++c) {
             if (e.bit[c] == -1) {
                 const int i = off + sm.slot[e.idx[c]];
-                a.gj[i] = gv[c];
-                static_cast<V *>(a.lphi)[t0 + e.idx[c]] = (V)(gv[c] / a.eps - bnew);
+                a.gj[i] = a.eps * gq[c];
+                const V lp = (V)(gq[c] - bnew);
+                static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
+                sm.lphi[e.idx[c]] = lp;
             }
         }
     } else if (a.mode == MODE_RESIDUAL) {
@@ -657,7 +954,8 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
             if (e.bit[c] == -1) {
                 const int i = off + sm.slot[e.idx[c]];
                 const double gg = a.gj[i];
-                const double marg = (gg == -INFINITY || lnM[c] == -INFINITY) ? 0.0 : exp(gg / a.eps + lnM[c]);
+                const double marg = (gg == -INFINITY || xM[c] == V(-INFINITY))
+                                        ? 0.0 : exp_acc<V>(gg * a.inv_eps + (base + (double)xM[c]));
                 acc += fabs(marg - a.muj[i]);
             }
         }
@@ -675,17 +973,348 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
         for (int c = 0; c < C; ++c) {
             if (e.bit[c] == -1) {
                 const int i = off + sm.slot[e.idx[c]];
+                const double lnMc = (xM[c] == V(-INFINITY)) ? -INFINITY : base + (double)xM[c];
                 double r;
                 if (a.mode == MODE_OUT_M)
-                    r = exp(lnM[c]);
+                    r = exp_acc<V>(lnMc);
                 else if (a.mode == MODE_OUT_PLAN)
-                    r = (a.gj[i] == -INFINITY) ? 0.0 : exp(a.gj[i] / a.eps + lnM[c]);
+                    r = (a.gj[i] == -INFINITY) ? 0.0 : exp_acc<V>(a.gj[i] * a.inv_eps + lnMc);
                 else
-                    r = lnM[c];
+                    r = lnMc;
                 a.out[i] = r;
             }
         }
     }
+    __syncthreads();
+}
+
+template <int NB, typename V, int NT, int C, int JCAP>
+__global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
+{
+    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smraw);
+    __shared__ int s_v;
+    if (threadIdx.x == 0) s_v = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int v = s_v;
+    if (v >= a.nt) return;
+    product_body<NB, V, NT, C, JCAP, true>(sm, a, v, v);
+}
+
+// Carry-free transfer operator of tile b for target j in one direction,
+// stored as scaled floats with the decay to the next tile base (processing
+// order) included:
+//   op[b][s][U] = T_b[s][U] exp(sum_{m in U} beta_m + gamma_{s+|U|} - gamma_s - w_{s+|U|} d)
+// where T_b is the composition of the thread operators (tile frame and
+// f-representation, provisional level scales gamma) and d the distance from
+// this tile's base to the next one, in units of eps.
+template <int NB, typename V, int NT, int C, int JCAP>
+__device__ void tile_operator(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const SweepArgs &a, int b, int n,
+                              int j, bool fwd)
+{
+    using En = Engine<NB, V, NT, C, JCAP, true>;
+    constexpr int NS = 1 << NB;
+    static_assert(NB * NS * (NT / 32) <= SweepSmem<NB, V, NT, C, JCAP, true>::GSZ, "operator scratch");
+    const int tid = threadIdx.x;
+    En e;
+    e.setup(sm, n, (V)a.span[b], fwd, j);
+    V op[NB][NS];
+    e.op_walk(op);
+    // composition in processing order (thread order is processing order in
+    // both directions, see Engine::setup): a shuffle tree inside each warp,
+    // then the warp results in order by warp 0
+    constexpr int NW = NT / 32;
+    const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        V Y[NB][NS], R[NB][NS];
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int U = 0; U < NS; ++U)
+                Y[s][U] = En::op_valid(s, U) ? __shfl_down_sync(0xffffffffu, op[s][U], o) : V(0);
+        En::op_compose(op, Y, R);
+        if ((lane & (2 * o - 1)) == 0) {
+#pragma unroll
+            for (int s = 0; s < NB; ++s)
+#pragma unroll
+                for (int U = 0; U < NS; ++U) op[s][U] = R[s][U];
+        }
+    }
+    V *scr = sm.G;   // [NW][NB][NS]
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int U = 0; U < NS; ++U) scr[(w * NB + s) * NS + U] = op[s][U];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int U = 0; U < NS; ++U) op[s][U] = scr[s * NS + U];
+        for (int q = 1; q < NW; ++q) {
+            V Y[NB][NS], R[NB][NS];
+#pragma unroll
+            for (int s = 0; s < NB; ++s)
+#pragma unroll
+                for (int U = 0; U < NS; ++U) Y[s][U] = scr[(q * NB + s) * NS + U];
+            En::op_compose(op, Y, R);
+#pragma unroll
+            for (int s = 0; s < NB; ++s)
+#pragma unroll
+                for (int U = 0; U < NS; ++U) op[s][U] = R[s][U];
+        }
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int U = 0; U < NS; ++U) scr[s * NS + U] = op[s][U];
+    }
+    __syncthreads();
+    // absolute scaled floats with the decay to the next base
+    double d = 0.0;
+    if (fwd) {
+        if (b + 1 < a.nt) d = a.ulb[b + 1] - a.ulb[b];
+    } else {
+        if (b >= 1) d = a.urb[b] - a.urb[b - 1];
+    }
+    SfT<V> *dst = sfp<V>(fwd ? a.opF : a.opB) + (size_t)b * NB * NS;
+    for (int idx = tid; idx < NB * NS; idx += NT) {
+        const int s = idx / NS, U = idx % NS;
+        if (!En::op_valid(s, U)) continue;
+        const int su = s + popc_c(U);
+        double gs = 0.0, gsu = 0.0, bu = 0.0;
+        for (int q = 0; q < su; ++q) {
+            if (q < s) gs += (double)sm.D[q];
+            gsu += (double)sm.D[q];
+        }
+        for (int k = 0; k < NB; ++k)
+            if ((U >> k) & 1) bu += sm.beta[k];
+        const double wsu = (double)su * (double)(NB + 1 - su);
+        const V val = scr[s * NS + U];
+        dst[idx] = sf_store(sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d));
+    }
+    __syncthreads();
+}
+
+template <int NB, typename V, int NT, int C, int JCAP>
+__global__ void __launch_bounds__(NT, 3) k_tileop(SweepArgs a)
+{
+    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smraw);
+    const int b = blockIdx.x;
+    const uint32_t t0 = a.tstart[b];
+    const int n = (int)(a.tstart[b + 1] - t0);
+    load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
+    tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.j, true);
+    tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.j, false);
+}
+
+template <int NB, typename V, int NT, int C, int JCAP>
+__global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
+{
+    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smraw);
+    const int b = blockIdx.x;
+    product_body<NB, V, NT, C, JCAP, false>(sm, a, b, b);
+    if (a.jnext >= 0) {
+        // operators of the next target from the updated potentials of this tile
+        const uint32_t t0 = a.tstart[b];
+        const int n = (int)(a.tstart[b + 1] - t0);
+        load_betas(sm, a, b, a.jnext);
+        __syncthreads();
+        tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, true);
+        tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, false);
+    }
+}
+
+// Exclusive carries of every tile from the tile operators: one block per
+// direction, levels in order; for level s each state is an affine recurrence
+//   E_T(next) = exp(-w_s d) E_T + sum_{S strictly inside T} E_S op[|S|][T\S]
+// (E_empty = 1), scanned over the tiles as (log multiplier, offset) pairs.
+template <int NB, typename V>
+__global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
+{
+    constexpr int NS = 1 << NB;
+    constexpr int NTB = 1024;
+    constexpr int NWB = NTB / 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    const bool fwd = (blockIdx.x == 0);
+    const SfT<V> *op = sfp<V>(fwd ? a.opF : a.opB);
+    const SfT<V> *pdec = sfp<V>(fwd ? a.pdecF : a.pdecB);
+    SfT<V> *E = sfp<V>(fwd ? a.fcarry : a.bcarry);
+    const int nt = a.nt, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int R = (nt + NTB - 1) / NTB;
+    const int v0 = min(nt, tid * R), v1 = min(nt, v0 + R);
+    __shared__ V s_am[NWB];
+    __shared__ int s_ak[NWB];
+    __shared__ V s_m[NWB][NS];
+    __shared__ int s_k[NWB][NS];
+    for (int v = v0; v < v1; ++v) {
+        const int b = fwd ? v : nt - 1 - v;
+        E[(size_t)b * NS] = sf_one_st<V>();
+    }
+    static_for<1, NB + 1>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        __syncthreads();
+        // offset of tile b for state T of level s, from the lower-level carries
+        auto offset = [&](int b, int T) -> Sf<V> {
+            Sf<V> acc = sf_load<V>(op[((size_t)b * NB + 0) * NS + T]);
+#pragma unroll
+            for (int S = 1; S < NS; ++S) {
+                if ((S & ~T) == 0 && S != T)
+                    acc = sf_add(acc, sf_mul(sf_load<V>(E[(size_t)b * NS + S]),
+                                             sf_load<V>(op[((size_t)b * NB + popc_c(S)) * NS + (T ^ S)])));
+            }
+            return acc;
+        };
+        // map of one tile: x -> dec * x + off; of a range: composition
+        Sf<V> am = Sf<V>{V(0.5), 1};   // multiplier (1)
+        Sf<V> bb[NS];
+#pragma unroll
+        for (int T = 0; T < NS; ++T) bb[T] = sf_zero<V>();
+        for (int v = v0; v < v1; ++v) {
+            const int b = fwd ? v : nt - 1 - v;
+            const Sf<V> dec = sf_load<V>(pdec[(size_t)b * (NB + 1) + s]);
+#pragma unroll
+            for (int T = 1; T < NS; ++T)
+                if (popc_c(T) == s) bb[T] = sf_add(sf_mul(bb[T], dec), offset(b, T));
+            am = sf_mul(am, dec);
+        }
+        // inclusive warp scan of the maps: (am1, b1) then (am2, b2) = (am1 am2, b1 am2 + b2)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Sf<V> oa;
+            oa.m = __shfl_up_sync(FULL, am.m, o);
+            oa.k = __shfl_up_sync(FULL, am.k, o);
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    Sf<V> ob;
+                    ob.m = __shfl_up_sync(FULL, bb[T].m, o);
+                    ob.k = __shfl_up_sync(FULL, bb[T].k, o);
+                    if (lane >= o) bb[T] = sf_add(sf_mul(ob, am), bb[T]);
+                }
+            }
+            if (lane >= o) am = sf_mul(oa, am);
+        }
+        if (lane == 31) {
+            s_am[w] = am.m;
+            s_ak[w] = am.k;
+#pragma unroll
+            for (int T = 1; T < NS; ++T)
+                if (popc_c(T) == s) {
+                    s_m[w][T] = bb[T].m;
+                    s_k[w][T] = bb[T].k;
+                }
+        }
+        // exclusive within the warp
+        Sf<V> exa;
+        exa.m = __shfl_up_sync(FULL, am.m, 1);
+        exa.k = __shfl_up_sync(FULL, am.k, 1);
+        if (lane == 0) exa = Sf<V>{V(0.5), 1};
+        Sf<V> exb[NS];
+#pragma unroll
+        for (int T = 1; T < NS; ++T) {
+            if (popc_c(T) == s) {
+                exb[T].m = __shfl_up_sync(FULL, bb[T].m, 1);
+                exb[T].k = __shfl_up_sync(FULL, bb[T].k, 1);
+                if (lane == 0) exb[T] = sf_zero<V>();
+            }
+        }
+        __syncthreads();
+        if (w == 0) {
+            Sf<V> wa = Sf<V>{s_am[lane], s_ak[lane]};
+            Sf<V> wb[NS];
+#pragma unroll
+            for (int T = 1; T < NS; ++T)
+                if (popc_c(T) == s) wb[T] = Sf<V>{s_m[lane][T], s_k[lane][T]};
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                Sf<V> oa;
+                oa.m = __shfl_up_sync(FULL, wa.m, o);
+                oa.k = __shfl_up_sync(FULL, wa.k, o);
+#pragma unroll
+                for (int T = 1; T < NS; ++T) {
+                    if (popc_c(T) == s) {
+                        Sf<V> ob;
+                        ob.m = __shfl_up_sync(FULL, wb[T].m, o);
+                        ob.k = __shfl_up_sync(FULL, wb[T].k, o);
+                        if (lane >= o) wb[T] = sf_add(sf_mul(ob, wa), wb[T]);
+                    }
+                }
+                if (lane >= o) wa = sf_mul(oa, wa);
+            }
+            // exclusive prefix of the warps (only the offsets are needed)
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    Sf<V> pb;
+                    pb.m = __shfl_up_sync(FULL, wb[T].m, 1);
+                    pb.k = __shfl_up_sync(FULL, wb[T].k, 1);
+                    if (lane == 0) pb = sf_zero<V>();
+                    s_m[lane][T] = pb.m;
+                    s_k[lane][T] = pb.k;
+                }
+            }
+        }
+        __syncthreads();
+        // carry into this thread's first tile: warp prefix through the lane prefix
+        Sf<V> cur[NS];
+#pragma unroll
+        for (int T = 1; T < NS; ++T) {
+            if (popc_c(T) == s) {
+                const Sf<V> pb = Sf<V>{s_m[w][T], s_k[w][T]};
+                cur[T] = sf_add(sf_mul(pb, exa), exb[T]);
+            }
+        }
+        for (int v = v0; v < v1; ++v) {
+            const int b = fwd ? v : nt - 1 - v;
+            const Sf<V> dec = sf_load<V>(pdec[(size_t)b * (NB + 1) + s]);
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    E[(size_t)b * NS + T] = sf_store(cur[T]);
+                    cur[T] = sf_add(sf_mul(cur[T], dec), offset(b, T));
+                }
+            }
+        }
+    });
+}
+
+template <int NB, typename V, int NT, int C, int JCAP>
+cudaError_t launch_tileop_impl(const SweepArgs &a, cudaStream_t st)
+{
+    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
+    auto kern = k_tileop<NB, V, NT, C, JCAP>;
+    const size_t sz = sizeof(Sm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nt, NT, sz, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NB, typename V, int NT, int C, int JCAP>
+cudaError_t launch_prod_impl(const SweepArgs &a, cudaStream_t st)
+{
+    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
+    auto kern = k_prod<NB, V, NT, C, JCAP>;
+    const size_t sz = sizeof(Sm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nt, NT, sz, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NB, typename V>
+cudaError_t launch_carry_impl(const SweepArgs &a, cudaStream_t st)
+{
+    k_carry<NB, V><<<2, 1024, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <int NB, typename V, int NT, int C, int JCAP>

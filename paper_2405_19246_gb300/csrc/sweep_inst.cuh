@@ -3,6 +3,28 @@
 #include "shapes.cuh"
 #include "sweep.cuh"
 
+// launchers of the three-phase design, defined for NB <= kMaxOpBits
+#define MMOT_INSTANTIATE_OPS(NB_, V_)                                                  \
+    namespace mmot {                                                                   \
+    template <>                                                                        \
+    cudaError_t launch_tileop<NB_, V_>(const SweepArgs &a, cudaStream_t s)             \
+    {                                                                                  \
+        using S = Shape<NB_, V_>;                                                      \
+        return launch_tileop_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                \
+    }                                                                                  \
+    template <>                                                                        \
+    cudaError_t launch_prod<NB_, V_>(const SweepArgs &a, cudaStream_t s)               \
+    {                                                                                  \
+        using S = Shape<NB_, V_>;                                                      \
+        return launch_prod_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                  \
+    }                                                                                  \
+    template <>                                                                        \
+    cudaError_t launch_carry<NB_, V_>(const SweepArgs &a, cudaStream_t s)              \
+    {                                                                                  \
+        return launch_carry_impl<NB_, V_>(a, s);                                       \
+    }                                                                                  \
+    }
+
 #define MMOT_INSTANTIATE(NB_)                                                          \
     namespace mmot {                                                                   \
     template <>                                                                        \

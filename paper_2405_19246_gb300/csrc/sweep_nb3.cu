@@ -1,3 +1,5 @@
 // Sweep kernels for l = 4 marginals (3 state bits).
 #include "sweep_inst.cuh"
 MMOT_INSTANTIATE(3)
+MMOT_INSTANTIATE_OPS(3, float)
+MMOT_INSTANTIATE_OPS(3, double)
