@@ -157,6 +157,35 @@ typedef struct {
 } mmot_plan_info;
 mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
 
+/* One marginal product without any device memory allocation.
+ *
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory: code running under a memory manager that owns the
+ * whole device budget (a framework's caching pool), plug-ins that must not
+ * change the process's allocation state, or latency-critical loops where the
+ * implicit synchronisation of cudaMalloc is not acceptable.  It computes what
+ * mmot_marginal computes on a plan (FP32 in-tile scans), for the potentials g
+ * passed in, without creating a plan and without calling cudaMalloc, cudaFree
+ * or any allocating library routine.
+ *
+ *   l, N, x, eps  as in mmot_plan_create (x host or device, sorted);
+ *   g             l pointers to the potentials g_k = eps ln phi_k (host or
+ *                 device; device when plan_marginal = 1);
+ *   k, plan_marginal  as in mmot_marginal (0: M_k, 1: phi_k M_k, 2: ln M_k);
+ *   out           N[k] FP64 values, device memory (caller-owned);
+ *   cuda_stream   stream to use (borrowed); the call synchronises it before
+ *                 returning.
+ * Limits: 2 <= l <= 5, sum N <= 2^19 points, at most 1024 tiles; larger
+ * problems return MMOT_ERR_RANGE with a message.  Working storage is one
+ * static 8 MiB device array per GPU, held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (for example from several host threads) race. */
+mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const double *const *x,
+                                  const double *const *g, double eps, int k, int plan_marginal,
+                                  double *out, void *cuda_stream);
+
 /* Destroy a plan; NULL-safe. */
 void mmot_destroy(mmot_plan p);
 

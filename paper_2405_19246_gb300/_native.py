@@ -29,7 +29,7 @@ MMOT_OPT_PROFILE = 4
 EXPORTED = [
     "mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve", "mmot_objective",
     "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
-    "mmot_get_profile", "mmot_get_info", "mmot_destroy", "mmot_last_error",
+    "mmot_get_profile", "mmot_get_info", "mmot_marginal_noalloc", "mmot_destroy", "mmot_last_error",
 ]
 
 
@@ -76,6 +76,7 @@ def lib():
         L.mmot_set_option.argtypes = [vp, i, i64]
         L.mmot_get_profile.argtypes = [vp, i, P(i64), P(d), i]
         L.mmot_get_info.argtypes = [vp, P(MmotPlanInfo)]
+        L.mmot_marginal_noalloc.argtypes = [i, P(i64), P(vp), P(vp), d, i, i, vp, vp]
         L.mmot_destroy.argtypes = [vp]
         L.mmot_destroy.restype = None
         L.mmot_last_error.argtypes = []

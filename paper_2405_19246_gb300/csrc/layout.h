@@ -1,0 +1,166 @@
+// Host-side layout of one problem: the merged order of all support points
+// and its tiling (shared by mmot_plan_create and mmot_marginal_noalloc).
+//
+// Merged order: all T = sum_k N_k points sorted by (x, marginal, index); ties
+// between marginals go to the lower marginal index first, the tie rule of the
+// order classes D_p (Eq. D_p).
+// Tiles: consecutive runs of the merged order with at most K points, at most
+// jcap points of any one marginal, and max_s w_s * (x_last - x_first)/eps at
+// most `limit` (w_s = s(l - s)).
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "mmot_internal.cuh"
+
+namespace mmot {
+
+struct HostLayout {
+    int l = 0;
+    int64_t T = 0;
+    int nt = 0;
+    std::vector<double> xm;                  // merged coordinates
+    std::vector<uint8_t> mid;                // marginal of each merged point
+    std::vector<uint32_t> mpos[MMOT_MAXL];   // merged index of each local point
+    std::vector<uint32_t> tstart;            // [nt+1]
+    std::vector<uint32_t> tile_of;           // tile of each merged point
+    std::vector<double> xlb, xrb;            // first / last x of each tile
+    std::vector<double> ulb, urb, span;      // the same divided by eps; span = urb - ulb
+    std::vector<double> pos;                 // (x_t - xlb[tile])/eps
+    std::vector<int32_t> cnt;                // [nt*l] points of marginal m before tile b
+    std::vector<int32_t> reftile;            // [nt*l] nearest tile holding points of m
+};
+
+inline void build_layout(int l, const int64_t *N, const std::vector<std::vector<double>> &hx, double eps,
+                         int K, int jcap, double limit, HostLayout &L)
+{
+    L.l = l;
+    int64_t T = 0;
+    for (int k = 0; k < l; ++k) T += N[k];
+    L.T = T;
+    L.xm.resize(T);
+    L.mid.resize(T);
+    for (int k = 0; k < l; ++k) L.mpos[k].resize(N[k]);
+    {
+        std::vector<int64_t> head(l, 0);
+        for (int64_t t = 0; t < T; ++t) {
+            int best = -1;
+            for (int k = 0; k < l; ++k) {
+                if (head[k] >= N[k]) continue;
+                if (best < 0 || hx[k][head[k]] < hx[best][head[best]]) best = k;
+            }
+            L.xm[t] = hx[best][head[best]];
+            L.mid[t] = (uint8_t)best;
+            L.mpos[best][head[best]] = (uint32_t)t;
+            head[best] += 1;
+        }
+    }
+    double wmax = 0.0;
+    for (int s = 0; s <= l; ++s) wmax = std::max(wmax, (double)s * (l - s));
+    L.tstart.clear();
+    {
+        int64_t t = 0;
+        std::vector<int> per(l, 0);
+        while (t < T) {
+            L.tstart.push_back((uint32_t)t);
+            const double x0 = L.xm[t];
+            std::fill(per.begin(), per.end(), 0);
+            per[L.mid[t]] = 1;
+            int64_t e = t + 1;
+            while (e < T && e - t < K && (L.xm[e] - x0) / eps * wmax <= limit && per[L.mid[e]] < jcap) {
+                per[L.mid[e]] += 1;
+                ++e;
+            }
+            t = e;
+        }
+        L.tstart.push_back((uint32_t)T);
+    }
+    const int nt = (int)L.tstart.size() - 1;
+    L.nt = nt;
+    L.tile_of.resize(T);
+    L.xlb.resize(nt);
+    L.xrb.resize(nt);
+    L.ulb.resize(nt);
+    L.urb.resize(nt);
+    L.span.resize(nt);
+    L.pos.resize(T);
+    L.cnt.assign((size_t)nt * l, 0);
+    L.reftile.assign((size_t)nt * l, -1);
+    std::vector<int32_t> run(l, 0);
+    for (int b = 0; b < nt; ++b) {
+        L.xlb[b] = L.xm[L.tstart[b]];
+        L.xrb[b] = L.xm[L.tstart[b + 1] - 1];
+        L.ulb[b] = L.xlb[b] / eps;
+        L.urb[b] = L.xrb[b] / eps;
+        L.span[b] = (L.xrb[b] - L.xlb[b]) / eps;
+        for (int k = 0; k < l; ++k) L.cnt[(size_t)b * l + k] = run[k];
+        for (uint32_t t = L.tstart[b]; t < L.tstart[b + 1]; ++t) {
+            L.pos[t] = (L.xm[t] - L.xlb[b]) / eps;
+            L.tile_of[t] = (uint32_t)b;
+            run[L.mid[t]] += 1;
+            L.reftile[(size_t)b * l + L.mid[t]] = b;
+        }
+    }
+    // tiles without points of marginal m use the nearest earlier tile that has
+    // some, else the nearest later one
+    for (int k = 0; k < l; ++k) {
+        int last = -1;
+        for (int b = 0; b < nt; ++b) {
+            int32_t &r = L.reftile[(size_t)b * l + k];
+            if (r == b) last = b;
+            else r = last;
+        }
+        int next = -1;
+        for (int b = nt - 1; b >= 0; --b) {
+            int32_t &r = L.reftile[(size_t)b * l + k];
+            if (r == b) next = b;
+            else if (r < 0) r = next;
+        }
+    }
+}
+
+// exp(-w_s d) from each tile base to the next base in processing order
+// (forward: left ends, backward: right ends), s = 0..NB, as scaled floats
+// m * 2^k stored as float2 (k in the bits of .y) or double2.
+inline void decay_tables(const HostLayout &L, int NB, bool fp64, std::vector<unsigned char> &F,
+                         std::vector<unsigned char> &B)
+{
+    const int nt = L.nt;
+    const int l = L.l;
+    const int NB1 = NB + 1;
+    const size_t sz = fp64 ? 16 : 8;
+    F.assign((size_t)nt * NB1 * sz, 0);
+    B.assign((size_t)nt * NB1 * sz, 0);
+    auto put = [&](std::vector<unsigned char> &dst, size_t idx, double lnv) {
+        const double y = lnv / std::log(2.0);
+        const bool zero = (y < -1.0e9);
+        const double n = std::floor(y);
+        int e = 0;
+        const double m = std::frexp(std::exp2(y - n), &e);
+        const long long k = (long long)n + e;
+        if (fp64) {
+            double *q = reinterpret_cast<double *>(dst.data()) + 2 * idx;
+            q[0] = zero ? 0.0 : m;
+            q[1] = zero ? 0.0 : (double)k;
+        } else {
+            float *q = reinterpret_cast<float *>(dst.data()) + 2 * idx;
+            const int ki = zero ? 0 : (int)k;
+            q[0] = zero ? 0.0f : (float)m;
+            std::memcpy(&q[1], &ki, sizeof(int));
+        }
+    };
+    for (int b = 0; b < nt; ++b) {
+        const double dF = (b + 1 < nt) ? L.ulb[b + 1] - L.ulb[b] : 0.0;
+        const double dB = (b >= 1) ? L.urb[b] - L.urb[b - 1] : 0.0;
+        for (int s = 0; s < NB1; ++s) {
+            const double ws = (double)s * (double)(l - s);
+            put(F, (size_t)b * NB1 + s, -ws * dF);
+            put(B, (size_t)b * NB1 + s, -ws * dB);
+        }
+    }
+}
+
+}  // namespace mmot

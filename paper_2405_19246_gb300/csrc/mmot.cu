@@ -26,6 +26,7 @@
 
 #include "../../include/mmot.h"
 #include "mmot_internal.cuh"
+#include "layout.h"
 #include "shapes.cuh"
 
 using namespace mmot;
@@ -33,6 +34,18 @@ using namespace mmot;
 namespace {
 
 thread_local std::string g_last_error;
+
+}  // namespace
+
+namespace mmot {
+mmot_status set_error(mmot_status st, const char *msg)
+{
+    g_last_error = msg;
+    return st;
+}
+}  // namespace mmot
+
+namespace {
 
 mmot_status fail(mmot_status st, const char *fmt, ...)
 {
@@ -216,7 +229,9 @@ cudaError_t launch_ops_nb(const SweepArgs &a, bool fp64, cudaStream_t st, int ki
     }
 }
 
-cudaError_t launch_ops(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
+}  // namespace
+
+cudaError_t mmot::launch_three_phase(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
 {
     switch (NB) {
     case 1: return launch_ops_nb<1>(a, fp64, st, kind);
@@ -225,6 +240,13 @@ cudaError_t launch_ops(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, i
     case 4: return launch_ops_nb<4>(a, fp64, st, kind);
     default: return cudaErrorInvalidValue;
     }
+}
+
+namespace {
+
+cudaError_t launch_ops(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
+{
+    return mmot::launch_three_phase(NB, a, fp64, st, kind);
 }
 
 template <int NB>
@@ -534,87 +556,20 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
         p->own_stream = true;
     }
 
-    // ---- merged order by (x, k, i) ----------------------------------------
-    std::vector<double> xm(T);
-    p->h_mid.resize(T);
-    for (int k = 0; k < l; ++k) p->h_mpos[k].resize(N[k]);
-    {
-        std::vector<int64_t> head(l, 0);
-        for (int64_t t = 0; t < T; ++t) {
-            int best = -1;
-            for (int k = 0; k < l; ++k) {
-                if (head[k] >= N[k]) continue;
-                if (best < 0 || hx[k][head[k]] < hx[best][head[best]]) best = k;
-            }
-            xm[t] = hx[best][head[best]];
-            p->h_mid[t] = (uint8_t)best;
-            p->h_mpos[best][head[best]] = (uint32_t)t;
-            head[best] += 1;
-        }
-    }
-
-    // ---- tiles: at most K points, at most jcap points of one marginal,
-    //      span * max_s w_s <= limit ---------------------------------------
-    double wmax = 0.0;
-    for (int s = 0; s <= l; ++s) wmax = std::max(wmax, (double)s * (l - s));
+    // ---- merged order and tiles (layout.h) ----------------------------------
     const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
-    std::vector<uint32_t> &ts = p->h_tstart;
-    ts.clear();
-    {
-        int64_t t = 0;
-        std::vector<int> per(l, 0);
-        while (t < T) {
-            ts.push_back((uint32_t)t);
-            const double x0 = xm[t];
-            std::fill(per.begin(), per.end(), 0);
-            per[p->h_mid[t]] = 1;
-            int64_t e = t + 1;
-            while (e < T && e - t < p->K && (xm[e] - x0) / eps * wmax <= limit && per[p->h_mid[e]] < jcap) {
-                per[p->h_mid[e]] += 1;
-                ++e;
-            }
-            t = e;
-        }
-        ts.push_back((uint32_t)T);
-    }
-    const int nt = (int)ts.size() - 1;
+    HostLayout L;
+    build_layout(l, N, hx, eps, p->K, jcap, limit, L);
+    const int nt = L.nt;
     p->nt = nt;
-    p->h_tile_of.resize(T);
-    std::vector<double> hxlb(nt), hxrb(nt);
-    std::vector<double> hspan(nt), hpos(T);
-    std::vector<int32_t> hcnt((size_t)nt * l), &href = p->h_reftile;
-    href.assign((size_t)nt * l, -1);
-    {
-        std::vector<int32_t> run(l, 0);
-        for (int b = 0; b < nt; ++b) {
-            hxlb[b] = xm[ts[b]];
-            hxrb[b] = xm[ts[b + 1] - 1];
-            hspan[b] = (hxrb[b] - hxlb[b]) / eps;
-            for (int k = 0; k < l; ++k) hcnt[(size_t)b * l + k] = run[k];
-            for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
-                hpos[t] = (xm[t] - hxlb[b]) / eps;
-                p->h_tile_of[t] = (uint32_t)b;
-                run[p->h_mid[t]] += 1;
-                href[(size_t)b * l + p->h_mid[t]] = b;
-            }
-        }
-        // tiles without points of marginal m use the nearest earlier tile
-        // that has some, else the nearest later one
-        for (int k = 0; k < l; ++k) {
-            int last = -1;
-            for (int b = 0; b < nt; ++b) {
-                int32_t &r = href[(size_t)b * l + k];
-                if (r == b) last = b;
-                else r = last;
-            }
-            int next = -1;
-            for (int b = nt - 1; b >= 0; --b) {
-                int32_t &r = href[(size_t)b * l + k];
-                if (r == b) next = b;
-                else if (r < 0) r = next;
-            }
-        }
-    }
+    p->h_mid = L.mid;
+    for (int k = 0; k < l; ++k) p->h_mpos[k] = L.mpos[k];
+    p->h_tstart = L.tstart;
+    p->h_tile_of = L.tile_of;
+    p->h_reftile = L.reftile;
+    std::vector<uint32_t> &ts = p->h_tstart;
+    std::vector<double> &hspan = L.span, &hpos = L.pos;
+    std::vector<int32_t> &hcnt = L.cnt, &href = p->h_reftile;
     p->h_beta.assign((size_t)nt * l, 0.0);
     for (int b = 0; b < nt; ++b)
         for (int k = 0; k < l; ++k) p->h_beta[(size_t)b * l + k] = -std::log((double)N[k]);
@@ -686,46 +641,13 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     ce = ce ? ce : up(p->mid, p->h_mid.data(), T);
     ce = ce ? ce : up(p->lphi, hl.data(), hl.size());
     ce = ce ? ce : up(p->tstart, ts.data(), sizeof(uint32_t) * (nt + 1));
-    std::vector<double> hulb(nt), hurb(nt);
-    for (int b = 0; b < nt; ++b) {
-        hulb[b] = hxlb[b] / eps;
-        hurb[b] = hxrb[b] / eps;
-    }
+    std::vector<double> &hulb = L.ulb, &hurb = L.urb;
     ce = ce ? ce : up(p->ulb, hulb.data(), sizeof(double) * nt);
     ce = ce ? ce : up(p->urb, hurb.data(), sizeof(double) * nt);
-    // exp(-w_s d) from each tile base to the next base in processing order, as
-    // scaled floats m * 2^k
+    // exp(-w_s d) from each tile base to the next base in processing order
     std::vector<unsigned char> hdecF, hdecB;
     if (p->three_phase) {
-        const int NB1 = p->NB + 1;
-        hdecF.assign((size_t)nt * NB1 * p->sfsz, 0);
-        hdecB.assign((size_t)nt * NB1 * p->sfsz, 0);
-        auto put = [&](std::vector<unsigned char> &dst, size_t idx, double lnv) {
-            const double y = lnv / std::log(2.0);
-            const double n = std::floor(y);
-            int e = 0;
-            const double m = std::frexp(std::exp2(y - n), &e);
-            const long long k = (long long)n + e;
-            if (fp64) {
-                double *q = reinterpret_cast<double *>(dst.data()) + 2 * idx;
-                q[0] = (y < -1.0e9) ? 0.0 : m;
-                q[1] = (y < -1.0e9) ? 0.0 : (double)k;
-            } else {
-                float *q = reinterpret_cast<float *>(dst.data()) + 2 * idx;
-                const int ki = (y < -1.0e9) ? 0 : (int)k;
-                q[0] = (y < -1.0e9) ? 0.0f : (float)m;
-                std::memcpy(&q[1], &ki, sizeof(int));
-            }
-        };
-        for (int b = 0; b < nt; ++b) {
-            const double dF = (b + 1 < nt) ? hulb[b + 1] - hulb[b] : 0.0;
-            const double dB = (b >= 1) ? hurb[b] - hurb[b - 1] : 0.0;
-            for (int sl = 0; sl < NB1; ++sl) {
-                const double ws = (double)sl * (double)(l - sl);
-                put(hdecF, (size_t)b * NB1 + sl, -ws * dF);
-                put(hdecB, (size_t)b * NB1 + sl, -ws * dB);
-            }
-        }
+        decay_tables(L, p->NB, fp64, hdecF, hdecB);
         ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
         ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());
     }

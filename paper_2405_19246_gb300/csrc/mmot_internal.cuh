@@ -101,6 +101,13 @@ cudaError_t launch_carry(const SweepArgs &a, cudaStream_t s);
 template <int NB, typename V>
 cudaError_t launch_prod(const SweepArgs &a, cudaStream_t s);
 constexpr int kMaxOpBits = 4;
+// message for mmot_last_error (defined in mmot.cu)
+}  // namespace mmot
+#include "../../include/mmot.h"
+namespace mmot {
+mmot_status set_error(mmot_status st, const char *msg);
+// kind: 2 tile operators, 3 carry scan, 4 tile products (defined in mmot.cu)
+cudaError_t launch_three_phase(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind);
 
 // Tile geometry chosen per (bits, precision): points per tile, threads,
 // maximum points of one marginal in a tile, and the tile span limit
