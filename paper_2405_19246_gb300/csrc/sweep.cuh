@@ -40,6 +40,8 @@
 #include <cstdint>
 #include <type_traits>
 
+#include <cuda_pipeline.h>
+
 #include "mmot_internal.cuh"
 
 namespace mmot {
@@ -120,17 +122,51 @@ struct Sf {
 template <typename V>
 __device__ __forceinline__ Sf<V> sf_zero() { return Sf<V>{V(0), 0}; }
 
+// x = m 2^k with 0.5 <= m < 1 (x >= 0).  FP32: read and set the exponent
+// field directly; subnormal x (far below every value that matters next to
+// the O(1) mantissas used here) is flushed to 0.
 template <typename V>
-__device__ __forceinline__ Sf<V> sf_make(V x)
+__device__ __forceinline__ Sf<V> sf_make(V x);
+template <>
+__device__ __forceinline__ Sf<float> sf_make<float>(float x)
 {
-    Sf<V> r;
-    if (x == V(0)) {
-        r.m = V(0);
+    const int bits = __float_as_int(x);
+    const int ef = (bits >> 23) & 0xff;
+    Sf<float> r;
+    if (ef == 0) {
+        r.m = 0.f;
         r.k = 0;
     } else {
-        r.m = vfrexp<V>(x, &r.k);
+        r.m = __int_as_float((bits & 0x807fffff) | (126 << 23));
+        r.k = ef - 126;
     }
     return r;
+}
+template <>
+__device__ __forceinline__ Sf<double> sf_make<double>(double x)
+{
+    Sf<double> r;
+    if (x == 0.0) {
+        r.m = 0.0;
+        r.k = 0;
+    } else {
+        r.m = frexp(x, &r.k);
+    }
+    return r;
+}
+
+// 2^d for d <= 0 (FP32: built from the exponent field; 0 below 2^-126)
+template <typename V>
+__device__ __forceinline__ V pow2neg(int d);
+template <>
+__device__ __forceinline__ float pow2neg<float>(int d)
+{
+    return (d < -126) ? 0.f : __int_as_float((d + 127) << 23);
+}
+template <>
+__device__ __forceinline__ double pow2neg<double>(int d)
+{
+    return (d < -1022) ? 0.0 : __longlong_as_double((long long)(d + 1023) << 52);
 }
 
 // a * exp(x) for an FP64 exponent x (x = -inf gives 0)
@@ -151,9 +187,14 @@ __device__ __forceinline__ Sf<V> sf_add(Sf<V> a, Sf<V> b)
 {
     if (a.m == V(0)) return b;
     if (b.m == V(0)) return a;
-    const int k = max(a.k, b.k);
-    Sf<V> r = sf_make<V>(vldexp<V>(a.m, a.k - k) + vldexp<V>(b.m, b.k - k));
-    r.k += k;
+    Sf<V> r;
+    if (a.k >= b.k) {
+        r = sf_make<V>(a.m + b.m * pow2neg<V>(b.k - a.k));
+        r.k += a.k;
+    } else {
+        r = sf_make<V>(b.m + a.m * pow2neg<V>(a.k - b.k));
+        r.k += b.k;
+    }
     return r;
 }
 
@@ -161,7 +202,9 @@ __device__ __forceinline__ Sf<V> sf_add(Sf<V> a, Sf<V> b)
 template <typename V>
 __device__ __forceinline__ V sf_value(Sf<V> a, int shift)
 {
-    return (a.m == V(0)) ? V(0) : vldexp<V>(a.m, a.k - shift);
+    if (a.m == V(0)) return V(0);
+    const int d = a.k - shift;
+    return (d <= 0) ? a.m * pow2neg<V>(d) : vldexp<V>(a.m, d);
 }
 
 // sum over the 32 lanes; every lane receives lane 0's result
@@ -173,7 +216,7 @@ __device__ __forceinline__ Sf<V> sf_warp_sum(Sf<V> a)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
     if (kmax == INT_MIN) return sf_zero<V>();
-    V m = (a.m == V(0)) ? V(0) : vldexp<V>(a.m, a.k - kmax);
+    V m = (a.m == V(0)) ? V(0) : a.m * pow2neg<V>(a.k - kmax);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const V y = __shfl_down_sync(FULL, m, o);
@@ -289,6 +332,7 @@ struct SweepSmem {
     static constexpr int OPSZ = (NB <= kMaxOpBits) ? NB * NS * (NT / 32) : 0;
     static constexpr int GSZ = (NS * JCAP > OPSZ) ? NS * JCAP : OPSZ;
     V G[WITH_G ? GSZ : 1];
+    double lmu[WITH_G ? JCAP : 1];   // ln mu of the tile's target points (prefetched)
 };
 
 // Per-thread engine: a contiguous chunk of C points of the tile, in the
@@ -821,6 +865,14 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
     if (sm.ntarget > JCAP) {
         if (tid == 0) atomicOr(a.err, ERR_RANGE);
     }
+    // prefetch ln mu of the target points (consecutive local indices) into
+    // shared memory; waited for before the epilogue
+    const int32_t off0 = a.cnt[(size_t)b * a.l + a.j];
+    if (a.mode == MODE_UPDATE) {
+        const int nq = min(sm.ntarget, JCAP);
+        for (int q = tid; q < nq; q += NT) __pipeline_memcpy_async(&sm.lmu[q], a.lnmuj + off0 + q, sizeof(double));
+    }
+    __pipeline_commit();
 
     En e;
     // ---- backward states inside the tile from the stored carry -------------
@@ -904,7 +956,9 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
     });
 
     // ---- FP64 epilogue ------------------------------------------------------
-    const int32_t off = a.cnt[(size_t)b * a.l + a.j];
+    const int32_t off = off0;
+    __pipeline_wait_prior(0);
+    __syncthreads();
     if (a.mode == MODE_UPDATE) {
         // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base) - xM   (FP64)
         double gq[C];
@@ -914,8 +968,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
         for (int c = 0; c < C; ++c) {
             gq[c] = -INFINITY;
             if (e.bit[c] == -1) {
-                const int i = off + sm.slot[e.idx[c]];
-                const double lm = a.lnmuj[i];
+                const double lm = sm.lmu[sm.slot[e.idx[c]]];
                 if (lm > -INFINITY) {
                     gq[c] = (lm - base) - (double)xM[c];
                     if (!isfinite(gq[c])) bad = true;
@@ -1137,7 +1190,7 @@ __global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
 //   E_T(next) = exp(-w_s d) E_T + sum_{S strictly inside T} E_S op[|S|][T\S]
 // (E_empty = 1), scanned over the tiles as (log multiplier, offset) pairs.
 template <int NB, typename V>
-__global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
+__global__ void __launch_bounds__(1024) k_carry_generic(SweepArgs a)
 {
     constexpr int NS = 1 << NB;
     constexpr int NTB = 1024;
@@ -1286,6 +1339,177 @@ __global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
     });
 }
 
+// Fast variant for nt <= 1024 * RM: each thread owns at most RM consecutive
+// tiles; per level, all loads of a thread's tiles are issued together and the
+// offsets stay in registers for the apply pass.
+template <int NB, typename V, int RM>
+__global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
+{
+    constexpr int NS = 1 << NB;
+    constexpr int NTB = 1024;
+    constexpr int NWB = NTB / 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    const bool fwd = (blockIdx.x == 0);
+    const SfT<V> *__restrict__ op = sfp<V>(fwd ? a.opF : a.opB);
+    const SfT<V> *__restrict__ pdec = sfp<V>(fwd ? a.pdecF : a.pdecB);
+    SfT<V> *E = sfp<V>(fwd ? a.fcarry : a.bcarry);
+    const int nt = a.nt, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int R = (nt + NTB - 1) / NTB;
+    const int v0 = min(nt, tid * R), v1 = min(nt, v0 + R);
+    __shared__ V s_am[NWB];
+    __shared__ int s_ak[NWB];
+    __shared__ V s_m[NWB][NS];
+    __shared__ int s_k[NWB][NS];
+    for (int v = v0; v < v1; ++v) {
+        const int b = fwd ? v : nt - 1 - v;
+        E[(size_t)b * NS] = sf_one_st<V>();
+    }
+    static_for<1, NB + 1>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        __syncthreads();
+        // pass 1: offsets and decays of this thread's tiles (loads only)
+        Sf<V> off[RM][NS];
+        Sf<V> dec[RM];
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const int v = v0 + r;
+            const bool ok = v < v1;
+            const int b = ok ? (fwd ? v : nt - 1 - v) : 0;
+            dec[r] = ok ? sf_load<V>(__ldg(pdec + (size_t)b * (NB + 1) + s)) : sf_zero<V>();
+            Sf<V> Elow[NS];
+#pragma unroll
+            for (int S = 1; S < NS; ++S)
+                Elow[S] = (ok && popc_c(S) < s) ? sf_load<V>(__ldcg(E + (size_t)b * NS + S)) : sf_zero<V>();
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    Sf<V> acc = ok ? sf_load<V>(__ldg(op + ((size_t)b * NB + 0) * NS + T)) : sf_zero<V>();
+#pragma unroll
+                    for (int S = 1; S < NS; ++S) {
+                        if ((S & ~T) == 0 && S != T) {
+                            const Sf<V> o = ok ? sf_load<V>(__ldg(op + ((size_t)b * NB + popc_c(S)) * NS + (T ^ S)))
+                                               : sf_zero<V>();
+                            acc = sf_add(acc, sf_mul(Elow[S], o));
+                        }
+                    }
+                    off[r][T] = acc;
+                }
+            }
+        }
+        // composition of the thread's maps
+        Sf<V> am = Sf<V>{V(0.5), 1};
+        Sf<V> bb[NS];
+#pragma unroll
+        for (int T = 0; T < NS; ++T) bb[T] = sf_zero<V>();
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            if (v0 + r < v1) {
+#pragma unroll
+                for (int T = 1; T < NS; ++T)
+                    if (popc_c(T) == s) bb[T] = sf_add(sf_mul(bb[T], dec[r]), off[r][T]);
+                am = sf_mul(am, dec[r]);
+            }
+        }
+        // inclusive warp scan of the maps: (am1, b1) then (am2, b2) = (am1 am2, b1 am2 + b2)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Sf<V> oa;
+            oa.m = __shfl_up_sync(FULL, am.m, o);
+            oa.k = __shfl_up_sync(FULL, am.k, o);
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    Sf<V> ob;
+                    ob.m = __shfl_up_sync(FULL, bb[T].m, o);
+                    ob.k = __shfl_up_sync(FULL, bb[T].k, o);
+                    if (lane >= o) bb[T] = sf_add(sf_mul(ob, am), bb[T]);
+                }
+            }
+            if (lane >= o) am = sf_mul(oa, am);
+        }
+        if (lane == 31) {
+            s_am[w] = am.m;
+            s_ak[w] = am.k;
+#pragma unroll
+            for (int T = 1; T < NS; ++T)
+                if (popc_c(T) == s) {
+                    s_m[w][T] = bb[T].m;
+                    s_k[w][T] = bb[T].k;
+                }
+        }
+        Sf<V> exa;
+        exa.m = __shfl_up_sync(FULL, am.m, 1);
+        exa.k = __shfl_up_sync(FULL, am.k, 1);
+        if (lane == 0) exa = Sf<V>{V(0.5), 1};
+        Sf<V> exb[NS];
+#pragma unroll
+        for (int T = 1; T < NS; ++T) {
+            if (popc_c(T) == s) {
+                exb[T].m = __shfl_up_sync(FULL, bb[T].m, 1);
+                exb[T].k = __shfl_up_sync(FULL, bb[T].k, 1);
+                if (lane == 0) exb[T] = sf_zero<V>();
+            }
+        }
+        __syncthreads();
+        if (w == 0) {
+            Sf<V> wa = Sf<V>{s_am[lane], s_ak[lane]};
+            Sf<V> wb[NS];
+#pragma unroll
+            for (int T = 1; T < NS; ++T)
+                if (popc_c(T) == s) wb[T] = Sf<V>{s_m[lane][T], s_k[lane][T]};
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                Sf<V> oa;
+                oa.m = __shfl_up_sync(FULL, wa.m, o);
+                oa.k = __shfl_up_sync(FULL, wa.k, o);
+#pragma unroll
+                for (int T = 1; T < NS; ++T) {
+                    if (popc_c(T) == s) {
+                        Sf<V> ob;
+                        ob.m = __shfl_up_sync(FULL, wb[T].m, o);
+                        ob.k = __shfl_up_sync(FULL, wb[T].k, o);
+                        if (lane >= o) wb[T] = sf_add(sf_mul(ob, wa), wb[T]);
+                    }
+                }
+                if (lane >= o) wa = sf_mul(oa, wa);
+            }
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    Sf<V> pb;
+                    pb.m = __shfl_up_sync(FULL, wb[T].m, 1);
+                    pb.k = __shfl_up_sync(FULL, wb[T].k, 1);
+                    if (lane == 0) pb = sf_zero<V>();
+                    s_m[lane][T] = pb.m;
+                    s_k[lane][T] = pb.k;
+                }
+            }
+        }
+        __syncthreads();
+        Sf<V> cur[NS];
+#pragma unroll
+        for (int T = 1; T < NS; ++T) {
+            if (popc_c(T) == s) cur[T] = sf_add(sf_mul(Sf<V>{s_m[w][T], s_k[w][T]}, exa), exb[T]);
+        }
+        // pass 2: apply (stores only)
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const int v = v0 + r;
+            if (v < v1) {
+                const int b = fwd ? v : nt - 1 - v;
+#pragma unroll
+                for (int T = 1; T < NS; ++T) {
+                    if (popc_c(T) == s) {
+                        E[(size_t)b * NS + T] = sf_store(cur[T]);
+                        cur[T] = sf_add(sf_mul(cur[T], dec[r]), off[r][T]);
+                    }
+                }
+            }
+        }
+        __threadfence_block();
+    });
+}
+
 template <int NB, typename V, int NT, int C, int JCAP>
 cudaError_t launch_tileop_impl(const SweepArgs &a, cudaStream_t st)
 {
@@ -1313,7 +1537,12 @@ cudaError_t launch_prod_impl(const SweepArgs &a, cudaStream_t st)
 template <int NB, typename V>
 cudaError_t launch_carry_impl(const SweepArgs &a, cudaStream_t st)
 {
-    k_carry<NB, V><<<2, 1024, 0, st>>>(a);
+    if (a.nt <= 1024 * 2)
+        k_carry<NB, V, 2><<<2, 1024, 0, st>>>(a);
+    else if (a.nt <= 1024 * 4)
+        k_carry<NB, V, 4><<<2, 1024, 0, st>>>(a);
+    else
+        k_carry_generic<NB, V><<<2, 1024, 0, st>>>(a);
     return cudaGetLastError();
 }
 
