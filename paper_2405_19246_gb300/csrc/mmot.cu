@@ -145,6 +145,8 @@ struct mmot_plan_s {
     unsigned char *agg = nullptr, *inc = nullptr, *bcarry = nullptr;
     unsigned char *fcarry = nullptr, *opF = nullptr, *opB = nullptr;
     unsigned char *pdecF = nullptr, *pdecB = nullptr;
+    int *cflags = nullptr;          // carry-scan chunk flags [2][32][NB+1]
+    unsigned char *cagg = nullptr;  // carry-scan chunk contributions [2][32][NS]
     size_t sfsz = 8;
     bool three_phase = false;  // tile operators + carry scan (l <= 5)
     int ops_target = -1;       // target whose tile operators are current
@@ -307,6 +309,8 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.opB = p->opB;
     a.pdecF = p->pdecF;
     a.pdecB = p->pdecB;
+    a.cflags = p->cflags;
+    a.cagg = p->cagg;
     a.jnext = -1;
     a.gj = p->g[j];
     a.lnmuj = p->lnmu[j];
@@ -357,6 +361,7 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
             if (s != MMOT_OK) return s;
             p->ops_target = j;
         }
+        CUDA_TRY(cudaMemsetAsync(p->cflags, 0, sizeof(int) * 2 * 32 * (p->NB + 1), p->st));
         s = timed_launch(p, 3, a, fp64);
         if (s != MMOT_OK) return s;
         a.jnext = (mode == MODE_UPDATE) ? jnext : -1;
@@ -617,6 +622,8 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
         PA(p->opB, (size_t)nt * p->NB * p->NS * p->sfsz);
         PA(p->pdecF, (size_t)nt * (p->NB + 1) * p->sfsz);
         PA(p->pdecB, (size_t)nt * (p->NB + 1) * p->sfsz);
+        PA(p->cflags, (size_t)2 * 32 * (p->NB + 1));
+        PA(p->cagg, (size_t)2 * 32 * p->NS * p->sfsz);
     }
     PA(p->partial, nt);
     p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);

@@ -77,6 +77,9 @@ struct SweepArgs {
     const void *pdecF;
     const void *pdecB;
     int jnext;                // target of the operators computed after an update (-1: none)
+    // carry scan over chunks of tiles: flags [2][G][NB+1], contributions [2][G][NS]
+    int *cflags;
+    void *cagg;
     // target marginal
     double *gj;               // [N_j] potentials (FP64)
     const double *lnmuj;      // [N_j] ln mu_j (-inf for zero weights)

@@ -199,6 +199,8 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     const size_t o_opB = take(sizeof(float2) * nt * NB * NS);
     const size_t o_fc = take(sizeof(float2) * nt * NS);
     const size_t o_bc = take(sizeof(float2) * nt * NS);
+    const size_t o_cfl = take(sizeof(int) * 2 * 32 * l);
+    const size_t o_cag = take(sizeof(float2) * 2 * 32 * NS);
     const size_t o_err = take(sizeof(int));
     if (off > kScratchBytes) return err_msg(MMOT_ERR_RANGE, "problem needs %zu scratch bytes > %zu", off, kScratchBytes);
     std::vector<unsigned char> stage(o_opF, 0);   // everything the host fills
@@ -219,6 +221,8 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     // the error word must start at zero on every call (the array keeps the
     // previous call's contents)
     NA_TRY(cudaMemsetAsync(scratch + o_err, 0, sizeof(int), st));
+    // the carry-scan flags must start at zero too
+    NA_TRY(cudaMemsetAsync(scratch + o_cfl, 0, sizeof(int) * 2 * 32 * l, st));
 
     // ---- kernels ---------------------------------------------------------------
     SweepArgs a;
@@ -227,7 +231,6 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     a.j = k;
     a.nt = nt;
     a.mode = mode;
-    a.spin_limit = 1;
     a.eps = eps;
     a.inv_eps = 1.0 / eps;
     a.tstart = reinterpret_cast<const uint32_t *>(scratch + o_ts);
@@ -249,6 +252,9 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     a.gj = const_cast<double *>(g[k]);
     a.out = out;
     a.err = reinterpret_cast<int *>(scratch + o_err);
+    a.cflags = reinterpret_cast<int *>(scratch + o_cfl);
+    a.cagg = scratch + o_cag;
+    a.spin_limit = 1 << 23;
     a.jnext = -1;
     for (int kind = 2; kind <= 4; ++kind) NA_TRY(launch_three_phase(NB, a, false, st, kind));
     int herr = 0;

@@ -1185,185 +1185,47 @@ __global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
     }
 }
 
-// Exclusive carries of every tile from the tile operators: one block per
-// direction, levels in order; for level s each state is an affine recurrence
+// Exclusive carries of every tile from the tile operators.  For level s each
+// state is an affine recurrence over the tiles in processing order,
 //   E_T(next) = exp(-w_s d) E_T + sum_{S strictly inside T} E_S op[|S|][T\S]
-// (E_empty = 1), scanned over the tiles as (log multiplier, offset) pairs.
-template <int NB, typename V>
-__global__ void __launch_bounds__(1024) k_carry_generic(SweepArgs a)
-{
-    constexpr int NS = 1 << NB;
-    constexpr int NTB = 1024;
-    constexpr int NWB = NTB / 32;
-    constexpr unsigned FULL = 0xffffffffu;
-    const bool fwd = (blockIdx.x == 0);
-    const SfT<V> *op = sfp<V>(fwd ? a.opF : a.opB);
-    const SfT<V> *pdec = sfp<V>(fwd ? a.pdecF : a.pdecB);
-    SfT<V> *E = sfp<V>(fwd ? a.fcarry : a.bcarry);
-    const int nt = a.nt, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int R = (nt + NTB - 1) / NTB;
-    const int v0 = min(nt, tid * R), v1 = min(nt, v0 + R);
-    __shared__ V s_am[NWB];
-    __shared__ int s_ak[NWB];
-    __shared__ V s_m[NWB][NS];
-    __shared__ int s_k[NWB][NS];
-    for (int v = v0; v < v1; ++v) {
-        const int b = fwd ? v : nt - 1 - v;
-        E[(size_t)b * NS] = sf_one_st<V>();
-    }
-    static_for<1, NB + 1>([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        __syncthreads();
-        // offset of tile b for state T of level s, from the lower-level carries
-        auto offset = [&](int b, int T) -> Sf<V> {
-            Sf<V> acc = sf_load<V>(op[((size_t)b * NB + 0) * NS + T]);
-#pragma unroll
-            for (int S = 1; S < NS; ++S) {
-                if ((S & ~T) == 0 && S != T)
-                    acc = sf_add(acc, sf_mul(sf_load<V>(E[(size_t)b * NS + S]),
-                                             sf_load<V>(op[((size_t)b * NB + popc_c(S)) * NS + (T ^ S)])));
-            }
-            return acc;
-        };
-        // map of one tile: x -> dec * x + off; of a range: composition
-        Sf<V> am = Sf<V>{V(0.5), 1};   // multiplier (1)
-        Sf<V> bb[NS];
-#pragma unroll
-        for (int T = 0; T < NS; ++T) bb[T] = sf_zero<V>();
-        for (int v = v0; v < v1; ++v) {
-            const int b = fwd ? v : nt - 1 - v;
-            const Sf<V> dec = sf_load<V>(pdec[(size_t)b * (NB + 1) + s]);
-#pragma unroll
-            for (int T = 1; T < NS; ++T)
-                if (popc_c(T) == s) bb[T] = sf_add(sf_mul(bb[T], dec), offset(b, T));
-            am = sf_mul(am, dec);
-        }
-        // inclusive warp scan of the maps: (am1, b1) then (am2, b2) = (am1 am2, b1 am2 + b2)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Sf<V> oa;
-            oa.m = __shfl_up_sync(FULL, am.m, o);
-            oa.k = __shfl_up_sync(FULL, am.k, o);
-#pragma unroll
-            for (int T = 1; T < NS; ++T) {
-                if (popc_c(T) == s) {
-                    Sf<V> ob;
-                    ob.m = __shfl_up_sync(FULL, bb[T].m, o);
-                    ob.k = __shfl_up_sync(FULL, bb[T].k, o);
-                    if (lane >= o) bb[T] = sf_add(sf_mul(ob, am), bb[T]);
-                }
-            }
-            if (lane >= o) am = sf_mul(oa, am);
-        }
-        if (lane == 31) {
-            s_am[w] = am.m;
-            s_ak[w] = am.k;
-#pragma unroll
-            for (int T = 1; T < NS; ++T)
-                if (popc_c(T) == s) {
-                    s_m[w][T] = bb[T].m;
-                    s_k[w][T] = bb[T].k;
-                }
-        }
-        // exclusive within the warp
-        Sf<V> exa;
-        exa.m = __shfl_up_sync(FULL, am.m, 1);
-        exa.k = __shfl_up_sync(FULL, am.k, 1);
-        if (lane == 0) exa = Sf<V>{V(0.5), 1};
-        Sf<V> exb[NS];
-#pragma unroll
-        for (int T = 1; T < NS; ++T) {
-            if (popc_c(T) == s) {
-                exb[T].m = __shfl_up_sync(FULL, bb[T].m, 1);
-                exb[T].k = __shfl_up_sync(FULL, bb[T].k, 1);
-                if (lane == 0) exb[T] = sf_zero<V>();
-            }
-        }
-        __syncthreads();
-        if (w == 0) {
-            Sf<V> wa = Sf<V>{s_am[lane], s_ak[lane]};
-            Sf<V> wb[NS];
-#pragma unroll
-            for (int T = 1; T < NS; ++T)
-                if (popc_c(T) == s) wb[T] = Sf<V>{s_m[lane][T], s_k[lane][T]};
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                Sf<V> oa;
-                oa.m = __shfl_up_sync(FULL, wa.m, o);
-                oa.k = __shfl_up_sync(FULL, wa.k, o);
-#pragma unroll
-                for (int T = 1; T < NS; ++T) {
-                    if (popc_c(T) == s) {
-                        Sf<V> ob;
-                        ob.m = __shfl_up_sync(FULL, wb[T].m, o);
-                        ob.k = __shfl_up_sync(FULL, wb[T].k, o);
-                        if (lane >= o) wb[T] = sf_add(sf_mul(ob, wa), wb[T]);
-                    }
-                }
-                if (lane >= o) wa = sf_mul(oa, wa);
-            }
-            // exclusive prefix of the warps (only the offsets are needed)
-#pragma unroll
-            for (int T = 1; T < NS; ++T) {
-                if (popc_c(T) == s) {
-                    Sf<V> pb;
-                    pb.m = __shfl_up_sync(FULL, wb[T].m, 1);
-                    pb.k = __shfl_up_sync(FULL, wb[T].k, 1);
-                    if (lane == 0) pb = sf_zero<V>();
-                    s_m[lane][T] = pb.m;
-                    s_k[lane][T] = pb.k;
-                }
-            }
-        }
-        __syncthreads();
-        // carry into this thread's first tile: warp prefix through the lane prefix
-        Sf<V> cur[NS];
-#pragma unroll
-        for (int T = 1; T < NS; ++T) {
-            if (popc_c(T) == s) {
-                const Sf<V> pb = Sf<V>{s_m[w][T], s_k[w][T]};
-                cur[T] = sf_add(sf_mul(pb, exa), exb[T]);
-            }
-        }
-        for (int v = v0; v < v1; ++v) {
-            const int b = fwd ? v : nt - 1 - v;
-            const Sf<V> dec = sf_load<V>(pdec[(size_t)b * (NB + 1) + s]);
-#pragma unroll
-            for (int T = 1; T < NS; ++T) {
-                if (popc_c(T) == s) {
-                    E[(size_t)b * NS + T] = sf_store(cur[T]);
-                    cur[T] = sf_add(sf_mul(cur[T], dec), offset(b, T));
-                }
-            }
-        }
-    });
-}
-
-// Fast variant for nt <= 1024 * RM: each thread owns at most RM consecutive
-// tiles; per level, all loads of a thread's tiles are issued together and the
-// offsets stay in registers for the apply pass.
+// (E_empty = 1).  Grid: G co-resident blocks per direction (blockIdx.y), each
+// owning a contiguous chunk of tiles; per level a block composes its chunk's
+// maps (block scan), publishes the chunk's contribution at the next chunk's
+// base, adds the contributions of all earlier chunks (at most 31, one warp
+// window, decays from the tile positions) and applies the result to its
+// tiles.  Waits are bounded; on timeout the error word is set.
 template <int NB, typename V, int RM>
-__global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
+__global__ void __launch_bounds__(256) k_carry(SweepArgs a)
 {
     constexpr int NS = 1 << NB;
-    constexpr int NTB = 1024;
+    constexpr int NTB = 256;
     constexpr int NWB = NTB / 32;
     constexpr unsigned FULL = 0xffffffffu;
-    const bool fwd = (blockIdx.x == 0);
+    const bool fwd = (blockIdx.y == 0);
+    const int G = gridDim.x, c = blockIdx.x;
     const SfT<V> *__restrict__ op = sfp<V>(fwd ? a.opF : a.opB);
     const SfT<V> *__restrict__ pdec = sfp<V>(fwd ? a.pdecF : a.pdecB);
     SfT<V> *E = sfp<V>(fwd ? a.fcarry : a.bcarry);
+    SfT<V> *cagg = sfp<V>(a.cagg) + (size_t)blockIdx.y * G * NS;
+    int *cflag = a.cflags + (size_t)blockIdx.y * G * (NB + 1);
     const int nt = a.nt, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int R = (nt + NTB - 1) / NTB;
-    const int v0 = min(nt, tid * R), v1 = min(nt, v0 + R);
+    const int Rc = (nt + G - 1) / G;                  // tiles per chunk
+    const int cv0 = min(nt, c * Rc), cv1 = min(nt, cv0 + Rc);
+    const int R = (cv1 - cv0 + NTB - 1) / NTB;        // tiles per thread (<= RM)
+    const int v0 = min(cv1, cv0 + tid * R), v1 = min(cv1, v0 + R);
+    auto tile_of = [&](int v) { return fwd ? v : nt - 1 - v; };
+    // base position of chunk q in processing order (units of eps)
+    auto chunk_base = [&](int q) -> double {
+        const int v = min(nt - 1, q * Rc);
+        return fwd ? a.ulb[tile_of(v)] : a.urb[tile_of(v)];
+    };
     __shared__ V s_am[NWB];
     __shared__ int s_ak[NWB];
     __shared__ V s_m[NWB][NS];
     __shared__ int s_k[NWB][NS];
-    for (int v = v0; v < v1; ++v) {
-        const int b = fwd ? v : nt - 1 - v;
-        E[(size_t)b * NS] = sf_one_st<V>();
-    }
+    __shared__ V s_em[NS];
+    __shared__ int s_ek[NS];
+    for (int v = v0; v < v1; ++v) E[(size_t)tile_of(v) * NS] = sf_one_st<V>();
     static_for<1, NB + 1>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         __syncthreads();
@@ -1374,7 +1236,7 @@ __global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
         for (int r = 0; r < RM; ++r) {
             const int v = v0 + r;
             const bool ok = v < v1;
-            const int b = ok ? (fwd ? v : nt - 1 - v) : 0;
+            const int b = ok ? tile_of(v) : 0;
             dec[r] = ok ? sf_load<V>(__ldg(pdec + (size_t)b * (NB + 1) + s)) : sf_zero<V>();
             Sf<V> Elow[NS];
 #pragma unroll
@@ -1396,7 +1258,7 @@ __global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
                 }
             }
         }
-        // composition of the thread's maps
+        // composition of the thread's maps: x -> am x + bb
         Sf<V> am = Sf<V>{V(0.5), 1};
         Sf<V> bb[NS];
 #pragma unroll
@@ -1410,7 +1272,7 @@ __global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
                 am = sf_mul(am, dec[r]);
             }
         }
-        // inclusive warp scan of the maps: (am1, b1) then (am2, b2) = (am1 am2, b1 am2 + b2)
+        // block scan of the maps (inclusive in the warp, then across warps)
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             Sf<V> oa;
@@ -1452,11 +1314,12 @@ __global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
         }
         __syncthreads();
         if (w == 0) {
-            Sf<V> wa = Sf<V>{s_am[lane], s_ak[lane]};
+            // warp prefixes (lanes < NWB) and the chunk total
+            Sf<V> wa = (lane < NWB) ? Sf<V>{s_am[lane], s_ak[lane]} : Sf<V>{V(0.5), 1};
             Sf<V> wb[NS];
 #pragma unroll
             for (int T = 1; T < NS; ++T)
-                if (popc_c(T) == s) wb[T] = Sf<V>{s_m[lane][T], s_k[lane][T]};
+                if (popc_c(T) == s) wb[T] = (lane < NWB) ? Sf<V>{s_m[lane][T], s_k[lane][T]} : sf_zero<V>();
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 Sf<V> oa;
@@ -1473,30 +1336,83 @@ __global__ void __launch_bounds__(1024) k_carry(SweepArgs a)
                 }
                 if (lane >= o) wa = sf_mul(oa, wa);
             }
+            // publish the chunk's contribution at the next chunk's base
+            int *myflag = cflag + (size_t)c * (NB + 1) + s;
 #pragma unroll
             for (int T = 1; T < NS; ++T) {
                 if (popc_c(T) == s) {
+                    Sf<V> tot;
+                    tot.m = __shfl_sync(FULL, wb[T].m, NWB - 1);
+                    tot.k = __shfl_sync(FULL, wb[T].k, NWB - 1);
+                    if (lane == 0) cagg[(size_t)c * NS + T] = sf_store(tot);
                     Sf<V> pb;
                     pb.m = __shfl_up_sync(FULL, wb[T].m, 1);
                     pb.k = __shfl_up_sync(FULL, wb[T].k, 1);
                     if (lane == 0) pb = sf_zero<V>();
-                    s_m[lane][T] = pb.m;
-                    s_k[lane][T] = pb.k;
+                    if (lane < NWB) {
+                        s_m[lane][T] = pb.m;
+                        s_k[lane][T] = pb.k;
+                    }
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release(myflag, 1);
+            // carry into this chunk: contributions of all earlier chunks
+            const double ws = (double)(s * (NB + 1 - s));
+            const double ub = chunk_base(c);
+            bool fail = false;
+            Sf<V> part[NS];
+#pragma unroll
+            for (int T = 0; T < NS; ++T) part[T] = sf_zero<V>();
+            if (lane < c) {
+                const int p = lane;
+                const int f = wait_flag(cflag + (size_t)p * (NB + 1) + s, a.err, a.spin_limit);
+                if (f < 0) {
+                    fail = true;
+                } else {
+                    const double d = fabs(ub - chunk_base(p + 1));
+#pragma unroll
+                    for (int T = 1; T < NS; ++T)
+                        if (popc_c(T) == s)
+                            part[T] = sf_scale_exp(sf_load<V>(__ldcg(cagg + (size_t)p * NS + T)), -ws * d);
+                }
+            }
+            if (__ballot_sync(FULL, fail)) {
+                if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+            }
+#pragma unroll
+            for (int T = 1; T < NS; ++T) {
+                if (popc_c(T) == s) {
+                    const Sf<V> t = sf_warp_sum(part[T]);
+                    if (lane == 0) {
+                        s_em[T] = t.m;
+                        s_ek[T] = t.k;
+                    }
                 }
             }
         }
         __syncthreads();
+        // this thread's carry: chunk carry through the warp prefix and the lane prefix
         Sf<V> cur[NS];
 #pragma unroll
         for (int T = 1; T < NS; ++T) {
-            if (popc_c(T) == s) cur[T] = sf_add(sf_mul(Sf<V>{s_m[w][T], s_k[w][T]}, exa), exb[T]);
+            if (popc_c(T) == s) {
+                // maps before this thread: warp prefix (s_am of warps before, stored as
+                // exclusive offsets in s_m/s_k) and the in-warp exclusive (exa, exb)
+                Sf<V> m = Sf<V>{V(0.5), 1};
+                for (int q = 0; q < w; ++q) m = sf_mul(m, Sf<V>{s_am[q], s_ak[q]});
+                const Sf<V> chunkin = sf_mul(Sf<V>{s_em[T], s_ek[T]}, sf_mul(m, exa));
+                const Sf<V> pre = sf_add(sf_mul(Sf<V>{s_m[w][T], s_k[w][T]}, exa), exb[T]);
+                cur[T] = sf_add(chunkin, pre);
+            }
         }
         // pass 2: apply (stores only)
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
             const int v = v0 + r;
             if (v < v1) {
-                const int b = fwd ? v : nt - 1 - v;
+                const int b = tile_of(v);
 #pragma unroll
                 for (int T = 1; T < NS; ++T) {
                     if (popc_c(T) == s) {
@@ -1534,15 +1450,26 @@ cudaError_t launch_prod_impl(const SweepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// chunks per direction (co-resident: 2 * G blocks)
+inline int carry_chunks(int nt) { return nt < 32 ? (nt > 0 ? nt : 1) : 32; }
+
 template <int NB, typename V>
 cudaError_t launch_carry_impl(const SweepArgs &a, cudaStream_t st)
 {
-    if (a.nt <= 1024 * 2)
-        k_carry<NB, V, 2><<<2, 1024, 0, st>>>(a);
-    else if (a.nt <= 1024 * 4)
-        k_carry<NB, V, 4><<<2, 1024, 0, st>>>(a);
+    const int G = carry_chunks(a.nt);
+    const int Rc = (a.nt + G - 1) / G;
+    const int R = (Rc + 255) / 256;
+    const dim3 grid(G, 2);
+    if (R <= 1)
+        k_carry<NB, V, 1><<<grid, 256, 0, st>>>(a);
+    else if (R <= 2)
+        k_carry<NB, V, 2><<<grid, 256, 0, st>>>(a);
+    else if (R <= 4)
+        k_carry<NB, V, 4><<<grid, 256, 0, st>>>(a);
+    else if (R <= 8)
+        k_carry<NB, V, 8><<<grid, 256, 0, st>>>(a);
     else
-        k_carry_generic<NB, V><<<2, 1024, 0, st>>>(a);
+        return cudaErrorInvalidConfiguration;   // more than 65536 tiles
     return cudaGetLastError();
 }
 
