@@ -157,6 +157,15 @@ struct mmot_plan_s {
     double *dsum = nullptr;  // reduction results
     double *scratch = nullptr;  // max N doubles
     cudaGraphExec_t graph = nullptr;
+    // objective sweeps (l state bits, no target), device scratch allocated on
+    // first use: tile operators, carries, decays and scan words
+    bool obj_ready = false;
+    std::vector<unsigned char> h_odecF, h_odecB;
+    unsigned char *o_opF = nullptr, *o_opB = nullptr, *o_fc = nullptr, *o_bc = nullptr;
+    unsigned char *o_decF = nullptr, *o_decB = nullptr, *o_cagg = nullptr, *o_agg = nullptr, *o_inc = nullptr;
+    int *o_cflags = nullptr, *o_flags = nullptr;
+    size_t o_flags_bytes = 0;
+    double *o_lnz = nullptr;   // [nt] ln Z seen by each tile
     std::vector<void *> allocs;
     // profiling: pairs of events around each kernel launch
     int profile = 0;
@@ -312,9 +321,10 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.cflags = p->cflags;
     a.cagg = p->cagg;
     a.jnext = -1;
-    a.gj = p->g[j];
-    a.lnmuj = p->lnmu[j];
-    a.muj = p->mu[j];
+    // j = l: no target marginal (objective sweeps)
+    a.gj = (j < p->l) ? p->g[j] : nullptr;
+    a.lnmuj = (j < p->l) ? p->lnmu[j] : nullptr;
+    a.muj = (j < p->l) ? p->mu[j] : nullptr;
     a.out = out;
     a.partial = p->partial;
     a.err = p->err;
@@ -375,6 +385,90 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
     if (s != MMOT_OK) return s;
     CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
     return timed_launch(p, 1, a, fp64);
+}
+
+template <int Lm>
+cudaError_t launch_obj_l(const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
+{
+    return fp64 ? launch_objective<Lm, double>(a, st, kind) : launch_objective<Lm, float>(a, st, kind);
+}
+
+cudaError_t launch_obj(int l, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
+{
+    switch (l) {
+    case 2: return launch_obj_l<2>(a, fp64, st, kind);
+    case 3: return launch_obj_l<3>(a, fp64, st, kind);
+    case 4: return launch_obj_l<4>(a, fp64, st, kind);
+    case 5: return launch_obj_l<5>(a, fp64, st, kind);
+    case 6: return launch_obj_l<6>(a, fp64, st, kind);
+    case 7: return launch_obj_l<7>(a, fp64, st, kind);
+    default: return cudaErrorInvalidValue;   // l = 8: not built (256 states)
+    }
+}
+
+mmot_status ensure_objective_scratch(mmot_plan p)
+{
+    if (p->obj_ready) return MMOT_OK;
+    const int l = p->l;
+    const size_t nt = (size_t)p->nt, ns = (size_t)1 << l, sf = p->sfsz;
+    CUDA_TRY(p->alloc(&p->o_bc, nt * ns * sf));
+    CUDA_TRY(p->alloc(&p->o_lnz, nt));
+    if (l <= kMaxOpBits) {
+        CUDA_TRY(p->alloc(&p->o_fc, nt * ns * sf));
+        CUDA_TRY(p->alloc(&p->o_opF, nt * l * ns * sf));
+        CUDA_TRY(p->alloc(&p->o_opB, nt * l * ns * sf));
+        CUDA_TRY(p->alloc(&p->o_decF, p->h_odecF.size()));
+        CUDA_TRY(p->alloc(&p->o_decB, p->h_odecB.size()));
+        CUDA_TRY(p->alloc(&p->o_cflags, (size_t)2 * 32 * (l + 1)));
+        CUDA_TRY(p->alloc(&p->o_cagg, (size_t)2 * 32 * ns * sf));
+        CUDA_TRY(cudaMemcpyAsync(p->o_decF, p->h_odecF.data(), p->h_odecF.size(), cudaMemcpyHostToDevice, p->st));
+        CUDA_TRY(cudaMemcpyAsync(p->o_decB, p->h_odecB.data(), p->h_odecB.size(), cudaMemcpyHostToDevice, p->st));
+    } else {
+        CUDA_TRY(p->alloc(&p->o_agg, nt * ns * sf));
+        CUDA_TRY(p->alloc(&p->o_inc, nt * ns * sf));
+        p->o_flags_bytes = sizeof(int) * (nt * (l + 1) + 1);
+        CUDA_TRY(p->alloc(&p->o_flags, nt * (l + 1) + 1));
+    }
+    p->obj_ready = true;
+    return MMOT_OK;
+}
+
+// W = <C, T> by the gap formula (objective.cuh): per-tile W/Z into
+// p->partial, their sum into p->dsum[0], ln Z of every tile into p->o_lnz.
+mmot_status enqueue_cost(mmot_plan p)
+{
+    mmot_status s = ensure_objective_scratch(p);
+    if (s != MMOT_OK) return s;
+    const int l = p->l;
+    const bool fp64 = (p->prec == MMOT_FP64);
+    SweepArgs a = make_args(p, l, MODE_OUT_M, p->o_lnz);
+    a.agg = p->o_agg;
+    a.inc = p->o_inc;
+    a.flags = p->o_flags;
+    a.counter = p->o_flags ? p->o_flags + (size_t)p->nt * (l + 1) : nullptr;
+    a.bcarry = p->o_bc;
+    a.fcarry = p->o_fc;
+    a.opF = p->o_opF;
+    a.opB = p->o_opB;
+    a.pdecF = p->o_decF;
+    a.pdecB = p->o_decB;
+    a.cflags = p->o_cflags;
+    a.cagg = p->o_cagg;
+    if (l <= kMaxOpBits) {
+        CUDA_TRY(launch_obj(l, a, fp64, p->st, 2));
+        CUDA_TRY(cudaMemsetAsync(p->o_cflags, 0, sizeof(int) * 2 * 32 * (l + 1), p->st));
+        CUDA_TRY(launch_obj(l, a, fp64, p->st, 3));
+        CUDA_TRY(launch_obj(l, a, fp64, p->st, 5));
+    } else {
+        CUDA_TRY(cudaMemsetAsync(p->o_flags, 0, p->o_flags_bytes, p->st));
+        CUDA_TRY(launch_obj(l, a, fp64, p->st, 0));
+        CUDA_TRY(cudaMemsetAsync(p->o_flags, 0, p->o_flags_bytes, p->st));
+        CUDA_TRY(launch_obj(l, a, fp64, p->st, 5));
+    }
+    k_sum_partials<<<1, 256, 0, p->st>>>(p->partial, p->nt, p->dsum, 0);
+    CUDA_TRY(cudaGetLastError());
+    p->launches += (l <= kMaxOpBits) ? 4 : 3;
+    return MMOT_OK;
 }
 
 // g_k = -eps ln N_k, beta = -ln N_k, lphi = 0
@@ -653,6 +747,7 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     ce = ce ? ce : up(p->urb, hurb.data(), sizeof(double) * nt);
     // exp(-w_s d) from each tile base to the next base in processing order
     std::vector<unsigned char> hdecF, hdecB;
+    if (l <= kMaxOpBits) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB);
     if (p->three_phase) {
         decay_tables(L, p->NB, fp64, hdecF, hdecB);
         ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
@@ -774,7 +869,16 @@ mmot_status mmot_objective(mmot_plan p, mmot_result *out)
     out->primal = P;
     out->dual = D + p->eps - p->eps * Z;
     out->W = NAN;
-    return MMOT_OK;
+    if (p->l > kMaxObjectiveL) return check_device_error(p);
+    // transport cost: sum over tiles of eps W_b / Z_b, times Z
+    mmot_status sc = enqueue_cost(p);
+    if (sc != MMOT_OK) return sc;
+    double wz = 0.0, lnz = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&wz, p->dsum, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaMemcpyAsync(&lnz, p->o_lnz, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    out->W = (lnz == -INFINITY) ? 0.0 : wz * std::exp(lnz);
+    return check_device_error(p);
 }
 
 mmot_status mmot_solve(mmot_plan p, double tol, int itr_max, mmot_result *out)

@@ -112,6 +112,14 @@ mmot_status set_error(mmot_status st, const char *msg);
 // kind: 2 tile operators, 3 carry scan, 4 tile products (defined in mmot.cu)
 cudaError_t launch_three_phase(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind);
 
+// Objective sweeps of l marginals (l state bits, no target; objective.cuh).
+// kind: 0 backward look-back sweep (l >= 5), 2 tile operators, 3 carry scan
+// (l <= 4), 5 objective kernel.
+template <int L, typename V>
+cudaError_t launch_objective(const SweepArgs &a, cudaStream_t s, int kind);
+// largest l with objective kernels (l = 8 would need 256 states per point)
+constexpr int kMaxObjectiveL = 7;
+
 // Tile geometry chosen per (bits, precision): points per tile, threads,
 // maximum points of one marginal in a tile, and the tile span limit
 // max_s w_s * span (keeps in-tile exponents small).

@@ -1,0 +1,198 @@
+// Transport cost W = <C, T> of the current plan (Eq. k-mmot distance).
+//
+// Gap formula: between consecutive points of the merged order every tuple
+// whose set S of marginals lies left of the gap pays |S|(l - |S|) per unit
+// length (for a tuple, sum_{i<k} |x_i - x_k| is the integral over y of
+// n(y)(l - n(y)), n(y) the number of its points left of y), so
+//   W = sum_t (x_t - x_{t-1}) sum_S w_|S| F_S(x_t^-) G_{S^c}(x_t, incl. t)
+// over all 2^l subsets S of the l marginals, F the forward states (Sec. 4.2
+// class sums grouped by subset) before point t and G the backward states
+// including it.  The sweeps are the ones of the marginal product with l state
+// bits and no target marginal; the rate of a state is again w_s = s(l - s).
+//
+// In the tile frame F_S G_{S^c} at any position carries exp(-w_s span), the
+// same for every point of the tile, so each tile yields, in FP64,
+//   partial[b] = eps * W_b / Z_b,  out[b] = ln Z
+// with W_b the tile's gap sum and Z_b = sum_S F_S G_{S^c} at the first gap of
+// the tile (Z_b is the total mass Z in the tile's scale; the ratio is W_b / Z).
+#pragma once
+#include "shapes.cuh"
+#include "sweep.cuh"
+
+namespace mmot {
+
+template <int NB, typename V, int NT, int C, int JCAP, bool LOOKBACK>
+__global__ void __launch_bounds__(NT) k_objective(SweepArgs a)
+{
+    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
+    using En = Engine<NB, V, NT, C, JCAP, true, NB>;
+    constexpr int NS = 1 << NB;
+    constexpr int FULLS = NS - 1;
+    constexpr int K = NT * C;
+    constexpr int NW = NT / 32;
+    static_assert(JCAP == K, "the objective keeps the backward states of every point");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smraw);
+    __shared__ int s_v;
+    __shared__ V s_ev[NB + 1];
+    __shared__ double s_base;
+    __shared__ V s_wm[NW];
+    __shared__ int s_wk[NW];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int v, b;
+    if constexpr (LOOKBACK) {
+        if (tid == 0) s_v = atomicAdd(a.counter, 1);
+        __syncthreads();
+        v = s_v;
+        if (v >= a.nt) return;
+        b = v;
+    } else {
+        b = v = blockIdx.x;
+    }
+    const uint32_t t0 = a.tstart[b];
+    const int n = (int)(a.tstart[b + 1] - t0);
+    const V span = (V)a.span[b];
+    load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
+
+    // ---- backward states including each point, kept for every point --------
+    En e;
+    e.setup(sm, n, span, false, a.j);
+    for (int S = tid; S < NS; S += NT) {
+        sm.E[S] = sf_load<V>(sfp<V>(a.bcarry)[(size_t)b * NS + S]);
+        sm.Eh[S] = sf_scale_exp(sm.E[S], -En::sum_beta(sm, S));
+    }
+    __syncthreads();
+    e.template all_levels<false>(sm, a, v, b, false);
+    e.template walk_each<false>([&](int c) {
+        const int id = e.idx[c];
+#pragma unroll(En::UNR)
+        for (int U = 0; U < NS; ++U) sm.G[U * K + id] = (U == 0) ? V(1) : (e.carry[U] + e.run[U]);
+    });
+    if (tid <= NB) sm.gamG[tid] = sm.gam[tid];
+    __syncthreads();
+
+    // ---- forward states --------------------------------------------------------
+    e.setup(sm, n, span, true, a.j);
+    if constexpr (LOOKBACK) {
+        e.template all_levels<true>(sm, a, v, b, true);
+    } else {
+        for (int S = tid; S < NS; S += NT) {
+            sm.E[S] = sf_load<V>(sfp<V>(a.fcarry)[(size_t)b * NS + S]);
+            sm.Eh[S] = sf_scale_exp(sm.E[S], -En::sum_beta(sm, S));
+        }
+        __syncthreads();
+        e.template all_levels<false>(sm, a, v, b, true);
+    }
+    // per-level exponents gamma^F_s + gamma^G_{l-s} - w_s span, relative to
+    // their maximum (FP64), and the tile's FP64 base
+    if (tid == 0) {
+        double d[NB + 1];
+        double gmx = -INFINITY;
+        for (int s = 0; s <= NB; ++s) {
+            d[s] = sm.gam[s] + sm.gamG[NB - s] - (double)En::rate(s) * (double)span;
+            gmx = fmax(gmx, d[s]);
+        }
+        double sb = 0.0;
+        for (int k = 0; k < NB; ++k) sb += sm.beta[k];
+        s_base = sb + gmx;
+        for (int s = 0; s <= NB; ++s) s_ev[s] = (V)fmax(d[s] - gmx, -1.0e30);
+    }
+    __syncthreads();
+    const V gap0 = (b > 0) ? (V)(a.ulb[b] - a.urb[b - 1]) : V(0);
+    Sf<V> accW = sf_zero<V>(), accZ = sf_zero<V>();
+    e.template walk_each<true>([&](int c) {
+        const int id = e.idx[c];
+        V X[NB + 1];
+#pragma unroll
+        for (int s = 0; s <= NB; ++s) X[s] = V(0);
+#pragma unroll(En::UNR)
+        for (int S = 0; S < NS; ++S) {
+            const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
+            X[popc_c(S)] += fS * sm.G[(FULLS ^ S) * K + id];
+        }
+        V emx = V(-INFINITY);
+#pragma unroll
+        for (int s = 0; s <= NB; ++s)
+            if (X[s] > V(0)) emx = (s_ev[s] > emx) ? s_ev[s] : emx;
+        if (!(emx > V(-INFINITY))) return;
+        V sw = V(0), sz = V(0);
+#pragma unroll
+        for (int s = 0; s <= NB; ++s) {
+            if (X[s] > V(0)) {
+                const V t = vexp<V>(s_ev[s] - emx) * X[s];
+                sw = fma(En::rate(s), t, sw);
+                sz += t;
+            }
+        }
+        const V dx = (id > 0) ? sm.pos[id] - sm.pos[id - 1] : gap0;
+        accW = sf_add(accW, sf_scale_exp(sf_make<V>(dx * sw), (double)emx));
+        if (id == 0) accZ = sf_scale_exp(sf_make<V>(sz), (double)emx);
+    });
+    const Sf<V> ws = sf_warp_sum(accW);
+    if (lane == 0) {
+        s_wm[w] = ws.m;
+        s_wk[w] = ws.k;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Sf<V> tot = sf_zero<V>();
+        for (int q = 0; q < NW; ++q) tot = sf_add(tot, Sf<V>{s_wm[q], s_wk[q]});
+        // thread 0 holds the first point of the tile (forward order)
+        if (accZ.m == V(0)) {
+            a.partial[b] = 0.0;
+            a.out[b] = -INFINITY;
+        } else {
+            const double r = (tot.m == V(0)) ? 0.0 : ldexp((double)tot.m / (double)accZ.m, tot.k - accZ.k);
+            a.partial[b] = a.eps * r;
+            a.out[b] = log((double)accZ.m) + (double)accZ.k * kLn2 + s_base;
+        }
+    }
+}
+
+template <int NB, typename V, int NT, int C, bool LOOKBACK>
+cudaError_t launch_objective_kernel(const SweepArgs &a, cudaStream_t st)
+{
+    constexpr int K = NT * C;
+    using Sm = SweepSmem<NB, V, NT, C, K, true>;
+    auto kern = k_objective<NB, V, NT, C, K, LOOKBACK>;
+    const size_t sz = sizeof(Sm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nt, NT, sz, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Objective kernels of l marginals on the tiling of the marginal product
+// (tile shape of l - 1 bits).  kind: 0 backward look-back sweep, 2 tile
+// operators, 3 carry scan, 5 objective (three-phase carries for l <= 4,
+// forward look-back otherwise).
+template <int Lm, typename V>
+cudaError_t launch_objective_impl(const SweepArgs &a, cudaStream_t st, int kind)
+{
+    using S = Shape<Lm - 1, V>;
+    constexpr bool THREE = (Lm <= kMaxOpBits);
+    if (kind == 5) return launch_objective_kernel<Lm, V, S::NT, S::C, !THREE>(a, st);
+    if constexpr (THREE) {
+        if (kind == 2) return launch_tileop_impl<Lm, V, S::NT, S::C, S::JCAP, Lm>(a, st);
+        if (kind == 3) return launch_carry_impl<Lm, V, Lm>(a, st);
+    } else {
+        if (kind == 0) return launch_bwd_impl<Lm, V, S::NT, S::C, S::JCAP, Lm>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mmot
+
+#define MMOT_INSTANTIATE_OBJECTIVE(L_)                                                  \
+    namespace mmot {                                                                   \
+    template <>                                                                        \
+    cudaError_t launch_objective<L_, float>(const SweepArgs &a, cudaStream_t s, int k) \
+    {                                                                                  \
+        return launch_objective_impl<L_, float>(a, s, k);                              \
+    }                                                                                  \
+    template <>                                                                        \
+    cudaError_t launch_objective<L_, double>(const SweepArgs &a, cudaStream_t s, int k)\
+    {                                                                                  \
+        return launch_objective_impl<L_, double>(a, s, k);                             \
+    }                                                                                  \
+    }

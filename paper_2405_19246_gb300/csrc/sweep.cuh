@@ -337,7 +337,9 @@ struct SweepSmem {
 
 // Per-thread engine: a contiguous chunk of C points of the tile, in the
 // processing order of the pass (forward: increasing x, backward: decreasing).
-template <int NB, typename V, int NT, int C, int JCAP, bool WITH_G>
+// NB state bits; L marginals in the cost (L = NB + 1 for a marginal product,
+// L = NB for the all-subset sweeps of the objective).
+template <int NB, typename V, int NT, int C, int JCAP, bool WITH_G, int L = NB + 1>
 struct Engine {
     static constexpr int NS = 1 << NB;
     static constexpr int K = NT * C;
@@ -356,7 +358,7 @@ struct Engine {
     V run[NS];      // running local sums of the current walk
 
     // rate w_s = s(l - s) with l = NB + 1
-    __device__ static constexpr V rate(int s) { return (V)(s * (NB + 1 - s)); }
+    __device__ static constexpr V rate(int s) { return (V)(s * (L - s)); }
     // provisional level shift of level s in a tile of the given span
     __device__ static V dshift(int s, V span)
     {
@@ -448,6 +450,24 @@ struct Engine {
         }
     }
 
+    // Walk the chunk calling on_point(c) at every injected point, before (PRE)
+    // or after its injection.
+    template <bool PRE, typename OnP>
+    __device__ __forceinline__ void walk_each(OnP &&on_point)
+    {
+#pragma unroll(UNR)
+        for (int S = 0; S < NS; ++S) run[S] = V(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int k = bit[c];
+            if (k >= 0) {
+                if constexpr (PRE) on_point(c);
+                inject_dispatch<NB>(k, c);
+                if constexpr (!PRE) on_point(c);
+            }
+        }
+    }
+
     __device__ static double sum_beta(const Sm &sm, int S)
     {
         double b = 0.0;
@@ -511,7 +531,7 @@ struct Engine {
     {
         const int lane = threadIdx.x & 31;
         constexpr int NQ = (NS + 31) / 32;
-        const double ws = (double)s * (double)(NB + 1 - s);
+        const double ws = (double)s * (double)(L - s);
         Sf<V> own[NQ], acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -787,11 +807,11 @@ __device__ void load_tile(SweepSmem<NB, V, NT, C, JCAP, WITH_G> &sm, const Sweep
     __syncthreads();
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 __global__ void __launch_bounds__(NT, 3) k_bwd(SweepArgs a)
 {
     using Sm = SweepSmem<NB, V, NT, C, JCAP, false>;
-    using En = Engine<NB, V, NT, C, JCAP, false>;
+    using En = Engine<NB, V, NT, C, JCAP, false, L>;
     constexpr int NS = 1 << NB;
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
@@ -1062,11 +1082,11 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
 // where T_b is the composition of the thread operators (tile frame and
 // f-representation, provisional level scales gamma) and d the distance from
 // this tile's base to the next one, in units of eps.
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 __device__ void tile_operator(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const SweepArgs &a, int b, int n,
                               int j, bool fwd)
 {
-    using En = Engine<NB, V, NT, C, JCAP, true>;
+    using En = Engine<NB, V, NT, C, JCAP, true, L>;
     constexpr int NS = 1 << NB;
     static_assert(NB * NS * (NT / 32) <= SweepSmem<NB, V, NT, C, JCAP, true>::GSZ, "operator scratch");
     const int tid = threadIdx.x;
@@ -1145,14 +1165,14 @@ __device__ void tile_operator(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swe
         }
         for (int k = 0; k < NB; ++k)
             if ((U >> k) & 1) bu += sm.beta[k];
-        const double wsu = (double)su * (double)(NB + 1 - su);
+        const double wsu = (double)su * (double)(L - su);
         const V val = scr[s * NS + U];
         dst[idx] = sf_store(sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d));
     }
     __syncthreads();
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 __global__ void __launch_bounds__(NT, 3) k_tileop(SweepArgs a)
 {
     using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
@@ -1162,8 +1182,8 @@ __global__ void __launch_bounds__(NT, 3) k_tileop(SweepArgs a)
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
     load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
-    tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.j, true);
-    tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.j, false);
+    tile_operator<NB, V, NT, C, JCAP, L>(sm, a, b, n, a.j, true);
+    tile_operator<NB, V, NT, C, JCAP, L>(sm, a, b, n, a.j, false);
 }
 
 template <int NB, typename V, int NT, int C, int JCAP>
@@ -1194,7 +1214,7 @@ __global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
 // base, adds the contributions of all earlier chunks (at most 31, one warp
 // window, decays from the tile positions) and applies the result to its
 // tiles.  Waits are bounded; on timeout the error word is set.
-template <int NB, typename V, int RM>
+template <int NB, typename V, int RM, int L = NB + 1>
 __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
 {
     constexpr int NS = 1 << NB;
@@ -1359,7 +1379,7 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
             __syncwarp();
             if (lane == 0) st_release(myflag, 1);
             // carry into this chunk: contributions of all earlier chunks
-            const double ws = (double)(s * (NB + 1 - s));
+            const double ws = (double)(s * (L - s));
             const double ub = chunk_base(c);
             bool fail = false;
             Sf<V> part[NS];
@@ -1426,11 +1446,11 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
     });
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 cudaError_t launch_tileop_impl(const SweepArgs &a, cudaStream_t st)
 {
     using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
-    auto kern = k_tileop<NB, V, NT, C, JCAP>;
+    auto kern = k_tileop<NB, V, NT, C, JCAP, L>;
     const size_t sz = sizeof(Sm);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
     if (e != cudaSuccess) return e;
@@ -1453,7 +1473,7 @@ cudaError_t launch_prod_impl(const SweepArgs &a, cudaStream_t st)
 // chunks per direction (co-resident: 2 * G blocks)
 inline int carry_chunks(int nt) { return nt < 32 ? (nt > 0 ? nt : 1) : 32; }
 
-template <int NB, typename V>
+template <int NB, typename V, int L = NB + 1>
 cudaError_t launch_carry_impl(const SweepArgs &a, cudaStream_t st)
 {
     const int G = carry_chunks(a.nt);
@@ -1461,23 +1481,23 @@ cudaError_t launch_carry_impl(const SweepArgs &a, cudaStream_t st)
     const int R = (Rc + 255) / 256;
     const dim3 grid(G, 2);
     if (R <= 1)
-        k_carry<NB, V, 1><<<grid, 256, 0, st>>>(a);
+        k_carry<NB, V, 1, L><<<grid, 256, 0, st>>>(a);
     else if (R <= 2)
-        k_carry<NB, V, 2><<<grid, 256, 0, st>>>(a);
+        k_carry<NB, V, 2, L><<<grid, 256, 0, st>>>(a);
     else if (R <= 4)
-        k_carry<NB, V, 4><<<grid, 256, 0, st>>>(a);
+        k_carry<NB, V, 4, L><<<grid, 256, 0, st>>>(a);
     else if (R <= 8)
-        k_carry<NB, V, 8><<<grid, 256, 0, st>>>(a);
+        k_carry<NB, V, 8, L><<<grid, 256, 0, st>>>(a);
     else
         return cudaErrorInvalidConfiguration;   // more than 65536 tiles
     return cudaGetLastError();
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 cudaError_t launch_bwd_impl(const SweepArgs &a, cudaStream_t st)
 {
     using Sm = SweepSmem<NB, V, NT, C, JCAP, false>;
-    auto kern = k_bwd<NB, V, NT, C, JCAP>;
+    auto kern = k_bwd<NB, V, NT, C, JCAP, L>;
     const size_t sz = sizeof(Sm);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
     if (e != cudaSuccess) return e;

@@ -72,6 +72,56 @@ def test_marginal_product_parity(Plan, prec, l, N, eps, ties, zeros):
     plan.close()
 
 
+OBJ_TOL = {"fp32": 2e-5, "fp64": 1e-11}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("l,N,eps,ties,zeros", CASES)
+def test_objective_parity(Plan, prec, l, N, eps, ties, zeros):
+    """W = <C, T> (gap formula over all 2^l subsets), mass, primal and dual
+    terms for random potentials against the oracle's all-subset sweep
+    (W is not computed for l = 8)."""
+    Ns = [N + 37 * k for k in range(l)]
+    xs, mus = wl.random_small(l, Ns, seed=300 + l, ties=ties, zeros=zeros, grid=N // 3)
+    gs = _rand_g(xs, eps, seed=50 + l)
+    plan = Plan(xs, mus, eps, precision=prec)
+    for k in range(l):
+        plan.set_potentials(k, gs[k])
+    got = plan.objective()
+    lnM, lnZ, W = oracle.allpass(xs, gs, eps)
+    marg = [np.exp(gs[k] / eps + lnM[k]) for k in range(l)]
+    Z = math.exp(lnZ)
+    primal = sum(float(np.dot(gs[k], marg[k])) for k in range(l))
+    dual = sum(float(np.dot(gs[k], mus[k])) for k in range(l)) + eps - eps * Z
+    res = sum(float(np.sum(np.abs(marg[k] - mus[k]))) for k in range(l))
+    tol = OBJ_TOL[prec]
+    if l == 8:
+        assert math.isnan(got["W"])
+    else:
+        assert abs(got["W"] - W) <= tol * abs(W), (got["W"], W)
+    assert abs(got["mass"] - Z) <= tol * Z, (got["mass"], Z)
+    scale = sum(float(np.dot(np.abs(gs[k]), marg[k])) for k in range(l))
+    assert abs(got["primal"] - primal) <= tol * scale, (got["primal"], primal)
+    assert abs(got["dual"] - dual) <= tol * (scale + eps), (got["dual"], dual)
+    assert abs(got["residual"] - res) <= tol * (res + Z), (got["residual"], res)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_solve_objective_matches_oracle_sinkhorn(Plan, prec):
+    """A short solve (20 iterations, l = 3): W, residual and mass against the
+    oracle's log-domain Sinkhorn run from the same start."""
+    xs, mus = wl.sorted_uniform_lognormal(l=3, N=1500, instance=9)
+    eps = 2e-2
+    ref = oracle.sinkhorn(xs, mus, eps, tol=0.0, itr_max=20)
+    plan = Plan(xs, mus, eps, precision=prec)
+    out = plan.solve(0.0, 20)
+    tol = 1e-4 if prec == "fp32" else 1e-9
+    assert abs(out["W"] - ref["W"]) <= tol * abs(ref["W"]), (out["W"], ref["W"])
+    assert abs(out["mass"] - ref["mass"]) <= tol, (out["mass"], ref["mass"])
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_sinkhorn_iterations_parity(Plan, prec):
     xs, mus = wl.sorted_uniform_lognormal(l=4, N=2000, instance=3)
