@@ -48,7 +48,10 @@ WORKLOADS = {
 
 # DRAM traffic per k_fwd launch from one ncu capture, tied to the kernel source
 # it was measured on (null when the source has changed since).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # dram__bytes_read.sum + dram__bytes_write.sum, one k_prod launch (cold cache)
+    ("large", "fp32", "k_prod", "769893257b6d1d71"): 46774016 + 17920,
+}
 
 
 def kernel_source_hash():
@@ -339,7 +342,7 @@ def main():
                     "includes": "plan creation from host buffers (merge, tiling, upload), solve, "
                                 "potential download"},
             "gpu_launches": r["launches"], "clocks": r["clocks"],
-            "result": {k: r["out"][k] for k in ("iters", "residual", "primal", "dual", "mass")}}
+            "result": {k: r["out"][k] for k in ("iters", "residual", "W", "primal", "dual", "mass")}}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
