@@ -190,6 +190,69 @@ mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const double *const *
 /* Destroy a plan; NULL-safe. */
 void mmot_destroy(mmot_plan p);
 
+/* ---- Batches of independent instances -------------------------------------
+ * The paper solves one instance at a time (Algorithm 1); a batch solves many
+ * independent instances together.  Instances with the same l are laid out one
+ * after another in one merged order whose tiles never straddle two instances
+ * and across whose boundaries no state is carried, so every kernel launch of
+ * a Sinkhorn iteration serves all instances of that l at once; each l forms a
+ * group with its own launch sequence, all on the batch's stream.  Each
+ * instance stops on its own: after every check its residual (marginals
+ * 1..l-1, as in mmot_sinkhorn_step) is compared with tol and a converged
+ * instance is frozen (no further updates; its potentials stay as they were
+ * at the check that found it converged). */
+typedef struct mmot_batch_s *mmot_batch;   /* opaque, owned by the library */
+
+/* Create a batch of n >= 1 instances.
+ *   l[i]         marginals of instance i (2..8).
+ *   N, x, mu     the instances' arguments of mmot_plan_create concatenated:
+ *                instance i owns entries o_i .. o_i + l[i] - 1 with
+ *                o_i = l[0] + ... + l[i-1]; x and mu are host pointers.
+ *   eps[i]       regularisation of instance i.
+ *   prec         as in mmot_plan_create, for all instances.
+ *   tile_points  upper bound on points per tile (0: the kernel's maximum);
+ *                smaller tiles trade per-tile work for more parallelism and
+ *                are chosen by an autotuner.
+ *   cuda_stream  stream to use (borrowed), NULL: the batch creates one.
+ * Potentials start at g = -eps ln N_k per instance. */
+mmot_status mmot_batch_create(int n, const int *l, const int64_t *N, const double *const *x,
+                              const double *const *mu, const double *eps, mmot_precision prec,
+                              int tile_points, void *cuda_stream, mmot_batch *out);
+
+/* Run n_iters Sinkhorn iterations on every instance not yet converged, then
+ * check each of them (residual <= tol freezes it).  *active_out (may be
+ * NULL) receives the number of instances still running. */
+mmot_status mmot_batch_step(mmot_batch b, int n_iters, double tol, int *active_out);
+
+/* Reset every instance to its initial potentials and unfreeze it. */
+mmot_status mmot_batch_reset(mmot_batch b);
+
+/* Solve every instance: reset, then steps of check_every iterations until
+ * all are converged or itr_max iterations have run.  results (n entries,
+ * may be NULL) receive per instance: iterations until convergence (or
+ * itr_max), its last checked residual, and W, primal, dual, mass as in
+ * mmot_objective.  Returns MMOT_ERR_NOT_CONVERGED (results filled) when some
+ * instance did not converge. */
+mmot_status mmot_batch_solve(mmot_batch b, double tol, int itr_max, int check_every, mmot_result *results);
+
+/* Iterations run, last checked residual and converged flag of instance i. */
+mmot_status mmot_batch_status(mmot_batch b, int i, int *iters, double *residual, int *converged);
+
+/* Potentials g_k of instance i (N_k FP64, host or device). */
+mmot_status mmot_batch_get_potentials(mmot_batch b, int i, int k, double *g_out);
+
+typedef struct {
+    int instances;
+    int groups;                /* distinct l                                    */
+    int64_t total_points;
+    int64_t tiles;
+    int64_t kernel_launches;   /* library kernels launched on this batch so far */
+} mmot_batch_info;
+mmot_status mmot_batch_get_info(mmot_batch b, mmot_batch_info *info);
+
+/* Destroy a batch; NULL-safe. */
+void mmot_batch_destroy(mmot_batch b);
+
 /* Message of the last error on this thread ("" if none). */
 const char *mmot_last_error(void);
 

@@ -29,7 +29,10 @@ MMOT_OPT_PROFILE = 4
 EXPORTED = [
     "mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve", "mmot_objective",
     "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
-    "mmot_get_profile", "mmot_get_info", "mmot_marginal_noalloc", "mmot_destroy", "mmot_last_error",
+    "mmot_get_profile", "mmot_get_info", "mmot_marginal_noalloc",
+    "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_status",
+    "mmot_batch_get_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
+    "mmot_destroy", "mmot_last_error",
 ]
 
 
@@ -43,6 +46,11 @@ class MmotPlanInfo(ctypes.Structure):
                 ("tile_points", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("launches_per_iteration", ctypes.c_int), ("precision", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int64)]
+
+
+class MmotBatchInfo(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int), ("groups", ctypes.c_int), ("total_points", ctypes.c_int64),
+                ("tiles", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
 
 class MmotError(RuntimeError):
@@ -77,12 +85,21 @@ def lib():
         L.mmot_get_profile.argtypes = [vp, i, P(i64), P(d), i]
         L.mmot_get_info.argtypes = [vp, P(MmotPlanInfo)]
         L.mmot_marginal_noalloc.argtypes = [i, P(i64), P(vp), P(vp), d, i, i, vp, vp]
+        L.mmot_batch_create.argtypes = [i, P(i), P(i64), P(vp), P(vp), P(d), i, i, vp, P(vp)]
+        L.mmot_batch_step.argtypes = [vp, i, d, P(i)]
+        L.mmot_batch_reset.argtypes = [vp]
+        L.mmot_batch_solve.argtypes = [vp, d, i, i, P(MmotResult)]
+        L.mmot_batch_status.argtypes = [vp, i, P(i), P(d), P(i)]
+        L.mmot_batch_get_potentials.argtypes = [vp, i, i, vp]
+        L.mmot_batch_get_info.argtypes = [vp, P(MmotBatchInfo)]
+        L.mmot_batch_destroy.argtypes = [vp]
         L.mmot_destroy.argtypes = [vp]
         L.mmot_destroy.restype = None
         L.mmot_last_error.argtypes = []
         L.mmot_last_error.restype = ctypes.c_char_p
         for name in EXPORTED[:-2]:
             getattr(L, name).restype = ctypes.c_int
+        L.mmot_batch_destroy.restype = None
         _lib = L
     return _lib
 

@@ -157,3 +157,97 @@ class Plan:
         inf = nat.MmotPlanInfo()
         nat.check(nat.lib().mmot_get_info(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+
+class Batch:
+    """Many independent instances solved together (host inputs).
+
+    instances: sequence of (xs, mus, eps) with xs, mus sequences of l numpy
+    arrays each (l may differ between instances).  Instances with the same l
+    share one launch sequence; each instance is frozen once its residual is
+    at most tol at a check.
+    """
+
+    def __init__(self, instances, precision="fp32", tile_points=0, stream=None):
+        ls, Ns, xp, mp, eps, keep = [], [], [], [], [], []
+        for xs, mus, e in instances:
+            if len(xs) != len(mus):
+                raise ValueError("xs and mus differ in length")
+            ls.append(len(xs))
+            for x, m in zip(xs, mus):
+                x = _host_f64(x)
+                m = _host_f64(m)
+                keep += [x, m]
+                Ns.append(len(x))
+                xp.append(x.ctypes.data)
+                mp.append(m.ctypes.data)
+            eps.append(float(e))
+        self.n = len(ls)
+        self.l = ls
+        self.N = []
+        o = 0
+        for li in ls:
+            self.N.append(Ns[o:o + li])
+            o += li
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        nat.check(nat.lib().mmot_batch_create(
+            self.n, (ctypes.c_int * self.n)(*ls), (ctypes.c_int64 * len(Ns))(*Ns),
+            (ctypes.c_void_p * len(xp))(*xp), (ctypes.c_void_p * len(mp))(*mp),
+            (ctypes.c_double * self.n)(*eps), _PREC[precision], int(tile_points), st, ctypes.byref(h)))
+        del keep
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().mmot_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def reset(self):
+        nat.check(nat.lib().mmot_batch_reset(self._h))
+
+    def step(self, n_iters, tol):
+        """n_iters iterations on the running instances, then a check; returns
+        the number of instances still running."""
+        a = ctypes.c_int()
+        nat.check(nat.lib().mmot_batch_step(self._h, int(n_iters), float(tol), ctypes.byref(a)))
+        return a.value
+
+    def solve(self, tol, itr_max, check_every=10, results=True):
+        """Solve all instances; list of per-instance result dicts (or None)."""
+        arr = (nat.MmotResult * self.n)() if results else None
+        st = nat.lib().mmot_batch_solve(self._h, float(tol), int(itr_max), int(check_every), arr)
+        if st not in (nat.MMOT_OK, 6):
+            nat.check(st)
+        if not results:
+            return None
+        return [dict(iters=r.iters, residual=r.residual, W=r.W, primal=r.primal, dual=r.dual,
+                     mass=r.mass) for r in arr]
+
+    def status(self, i):
+        it, res, cv = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        nat.check(nat.lib().mmot_batch_status(self._h, int(i), ctypes.byref(it), ctypes.byref(res),
+                                              ctypes.byref(cv)))
+        return dict(iters=it.value, residual=res.value, converged=bool(cv.value))
+
+    def get_potentials(self, i, k):
+        g = np.empty(self.N[i][k], dtype=np.float64)
+        nat.check(nat.lib().mmot_batch_get_potentials(self._h, int(i), int(k), g.ctypes.data))
+        return g
+
+    def info(self):
+        inf = nat.MmotBatchInfo()
+        nat.check(nat.lib().mmot_batch_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}

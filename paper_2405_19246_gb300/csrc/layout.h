@@ -122,11 +122,43 @@ inline void build_layout(int l, const int64_t *N, const std::vector<std::vector<
     }
 }
 
+// Append the layout of one more instance (batches): merged indices, tiles and
+// the per-marginal counts move by the sizes already present; marg_off[k] is
+// the number of points of marginal k before the instance.
+inline void append_layout(HostLayout &D, const HostLayout &S, const int64_t *marg_off)
+{
+    const uint32_t toff = (uint32_t)D.T;
+    const int32_t boff = D.nt;
+    const int l = S.l;
+    D.l = l;
+    D.mid.insert(D.mid.end(), S.mid.begin(), S.mid.end());
+    D.pos.insert(D.pos.end(), S.pos.begin(), S.pos.end());
+    for (int k = 0; k < l; ++k)
+        for (uint32_t t : S.mpos[k]) D.mpos[k].push_back(t + toff);
+    if (!D.tstart.empty()) D.tstart.pop_back();
+    for (uint32_t t : S.tstart) D.tstart.push_back(t + toff);
+    for (uint32_t b : S.tile_of) D.tile_of.push_back(b + (uint32_t)boff);
+    D.xlb.insert(D.xlb.end(), S.xlb.begin(), S.xlb.end());
+    D.xrb.insert(D.xrb.end(), S.xrb.begin(), S.xrb.end());
+    D.ulb.insert(D.ulb.end(), S.ulb.begin(), S.ulb.end());
+    D.urb.insert(D.urb.end(), S.urb.begin(), S.urb.end());
+    D.span.insert(D.span.end(), S.span.begin(), S.span.end());
+    for (int b = 0; b < S.nt; ++b)
+        for (int k = 0; k < l; ++k) {
+            D.cnt.push_back(S.cnt[(size_t)b * l + k] + (int32_t)marg_off[k]);
+            D.reftile.push_back(S.reftile[(size_t)b * l + k] + boff);
+        }
+    D.T += S.T;
+    D.nt += S.nt;
+}
+
 // exp(-w_s d) from each tile base to the next base in processing order
 // (forward: left ends, backward: right ends), s = 0..NB, as scaled floats
-// m * 2^k stored as float2 (k in the bits of .y) or double2.
+// m * 2^k stored as float2 (k in the bits of .y) or double2.  The decay out
+// of the last tile, and across the boundary between two instances of a batch
+// (seg, one entry per tile, may be empty), is 0: no state crosses it.
 inline void decay_tables(const HostLayout &L, int NB, bool fp64, std::vector<unsigned char> &F,
-                         std::vector<unsigned char> &B)
+                         std::vector<unsigned char> &B, const std::vector<int32_t> &seg = {})
 {
     const int nt = L.nt;
     const int l = L.l;
@@ -136,10 +168,10 @@ inline void decay_tables(const HostLayout &L, int NB, bool fp64, std::vector<uns
     B.assign((size_t)nt * NB1 * sz, 0);
     auto put = [&](std::vector<unsigned char> &dst, size_t idx, double lnv) {
         const double y = lnv / std::log(2.0);
-        const bool zero = (y < -1.0e9);
-        const double n = std::floor(y);
+        const bool zero = !(y >= -1.0e9);
+        const double n = zero ? 0.0 : std::floor(y);
         int e = 0;
-        const double m = std::frexp(std::exp2(y - n), &e);
+        const double m = std::frexp(std::exp2(zero ? 0.0 : y - n), &e);
         const long long k = (long long)n + e;
         if (fp64) {
             double *q = reinterpret_cast<double *>(dst.data()) + 2 * idx;
@@ -152,13 +184,16 @@ inline void decay_tables(const HostLayout &L, int NB, bool fp64, std::vector<uns
             std::memcpy(&q[1], &ki, sizeof(int));
         }
     };
+    auto same = [&](int b0, int b1) { return seg.empty() || seg[b0] == seg[b1]; };
     for (int b = 0; b < nt; ++b) {
-        const double dF = (b + 1 < nt) ? L.ulb[b + 1] - L.ulb[b] : 0.0;
-        const double dB = (b >= 1) ? L.urb[b] - L.urb[b - 1] : 0.0;
+        const bool okF = (b + 1 < nt) && same(b, b + 1);
+        const bool okB = (b >= 1) && same(b - 1, b);
+        const double dF = okF ? L.ulb[b + 1] - L.ulb[b] : 0.0;
+        const double dB = okB ? L.urb[b] - L.urb[b - 1] : 0.0;
         for (int s = 0; s < NB1; ++s) {
             const double ws = (double)s * (double)(l - s);
-            put(F, (size_t)b * NB1 + s, -ws * dF);
-            put(B, (size_t)b * NB1 + s, -ws * dB);
+            put(F, (size_t)b * NB1 + s, okF ? -ws * dF : -INFINITY);
+            put(B, (size_t)b * NB1 + s, okB ? -ws * dB : -INFINITY);
         }
     }
 }

@@ -61,9 +61,11 @@ mmot_status fail(mmot_status st, const char *fmt, ...)
 #define CUDA_TRY(call)                                                                        \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError(); /* do not leave a non-sticky error for the next check */      \
             return fail(e_ == cudaErrorMemoryAllocation ? MMOT_ERR_OOM : MMOT_ERR_CUDA,       \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                     \
     } while (0)
 
 bool is_device_ptr(const void *p)
@@ -105,6 +107,14 @@ __global__ void k_sum_partials(const double *partial, int n, double *out, int ac
 
 }  // namespace
 
+// One problem instance as given to plan creation (host or device pointers).
+struct InstanceIn {
+    const int64_t *N = nullptr;
+    const double *const *x = nullptr;
+    const double *const *mu = nullptr;
+    double eps = 0.0;
+};
+
 struct mmot_plan_s {
     int l = 0;
     int64_t N[MMOT_MAXL] = {0};
@@ -128,6 +138,21 @@ struct mmot_plan_s {
     std::vector<uint32_t> h_tstart;
     std::vector<int32_t> h_reftile;
     std::vector<double> h_beta;
+    std::vector<double> h_beta0;   // baselines of the initial potentials
+    // batches: instances laid out one after the other (nseg = 1: single problem)
+    int nseg = 1;
+    bool batch = false;               // created by mmot_batch_create
+    std::vector<int32_t> seg_tile0;   // [nseg+1] first tile of each instance
+    std::vector<int64_t> seg_off;     // [(nseg+1)*l] first local index of instance q in marginal k
+    std::vector<double> seg_eps;      // [nseg]
+    std::vector<int64_t> seg_N;       // [nseg*l]
+    int32_t *d_seg = nullptr;         // [nt] instance of each tile
+    double *d_teps = nullptr;         // [nt] eps of each tile
+    int32_t *d_frozen = nullptr;      // [nseg] converged instances (no more updates)
+    int32_t *d_segt0 = nullptr;       // [nseg+1]
+    double *d_res = nullptr;          // [nseg] per-instance residuals
+    int64_t *d_goff = nullptr;        // [(nseg+1)*l] copy of seg_off
+    double *d_g0 = nullptr;           // [nseg*l] initial potential value per instance and marginal
     // device
     void *pos = nullptr;     // FP32 or FP64 (esz bytes per point)
     uint8_t *mid = nullptr;
@@ -328,6 +353,9 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.out = out;
     a.partial = p->partial;
     a.err = p->err;
+    a.seg = p->d_seg;
+    a.teps = p->d_teps;
+    a.frozen = p->d_frozen;
     return a;
 }
 
@@ -366,7 +394,10 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
     const bool fp64 = (p->prec == MMOT_FP64);
     if (p->three_phase) {
         mmot_status s;
-        if (p->ops_target != j) {
+        // batches: tiles of frozen instances skip the fused operator update, so
+        // products that read every tile start from fresh operators
+        const bool all_tiles = (p->batch && mode != MODE_UPDATE && mode != MODE_RESIDUAL);
+        if (p->ops_target != j || all_tiles) {
             s = timed_launch(p, 2, a, fp64);
             if (s != MMOT_OK) return s;
             p->ops_target = j;
@@ -478,6 +509,31 @@ __global__ void k_reset(double *g, int64_t n, double v)
         g[i] = v;
 }
 
+// g_k of instance q (one block per instance) = its initial value
+__global__ void k_reset_seg(double *g, const int64_t *off, const double *g0, int k, int l)
+{
+    const int q = blockIdx.x;
+    const int64_t i0 = off[(size_t)q * l + k], i1 = off[(size_t)(q + 1) * l + k];
+    const double v = g0[(size_t)q * l + k];
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) g[i] = v;
+}
+
+// res[q] (+)= sum of the per-tile partial sums of instance q (one thread per
+// instance, compensated)
+__global__ void k_seg_sum(const double *partial, const int32_t *t0, int nseg, double *res, int accumulate)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nseg) return;
+    double sum = 0.0, c = 0.0;
+    for (int b = t0[q]; b < t0[q + 1]; ++b) {
+        const double y = partial[b] - c;
+        const double t = sum + y;
+        c = (t - sum) - y;
+        sum = t;
+    }
+    res[q] = accumulate ? res[q] + sum : sum;
+}
+
 // One Gauss-Seidel iteration.  In the three-phase design it expects the tile
 // operators of target 0 to be current and leaves them current.
 mmot_status enqueue_iteration(mmot_plan p)
@@ -575,61 +631,82 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
     return MMOT_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-const char *mmot_last_error(void) { return g_last_error.c_str(); }
-
-void mmot_destroy(mmot_plan p)
+// Plan of one instance, or of a batch of independent instances with the same
+// l laid out one after the other (tiles never straddle two instances).
+mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision prec, int inputs_on_device,
+                       void *cuda_stream, mmot_plan *out, int tile_points = 0, bool batch = false)
 {
-    if (!p) return;
-    if (p->st) cudaStreamSynchronize(p->st);
-    delete p;
-}
-
-mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, const double *const *mu,
-                             double eps, mmot_precision prec, int inputs_on_device, void *cuda_stream,
-                             mmot_plan *out)
-{
-    g_last_error.clear();
-    if (!out) return fail(MMOT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (l < 2 || l > MMOT_MAXL) return fail(MMOT_ERR_INVALID_ARG, "l = %d outside [2, 8]", l);
-    if (!N || !x || !mu) return fail(MMOT_ERR_INVALID_ARG, "N, x or mu is NULL");
-    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(MMOT_ERR_INVALID_ARG, "eps must be positive and finite");
     if (prec != MMOT_FP64 && prec != MMOT_FP32_SCAN_FP64_POT)
         return fail(MMOT_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    const int nin = (int)ins.size();
+    if (nin < 1) return fail(MMOT_ERR_INVALID_ARG, "no instance");
     int64_t T = 0;
-    for (int k = 0; k < l; ++k) {
-        if (N[k] < 1) return fail(MMOT_ERR_INVALID_ARG, "N[%d] = %lld < 1", k, (long long)N[k]);
-        if (!x[k] || !mu[k]) return fail(MMOT_ERR_INVALID_ARG, "x[%d] or mu[%d] is NULL", k, k);
-        T += N[k];
+    int64_t N[MMOT_MAXL] = {0};
+    for (int q = 0; q < nin; ++q) {
+        const InstanceIn &in = ins[q];
+        if (!(in.eps > 0.0) || !std::isfinite(in.eps))
+            return fail(MMOT_ERR_INVALID_ARG, "instance %d: eps must be positive and finite", q);
+        for (int k = 0; k < l; ++k) {
+            if (in.N[k] < 1) return fail(MMOT_ERR_INVALID_ARG, "instance %d: N[%d] = %lld < 1", q, k, (long long)in.N[k]);
+            if (!in.x[k] || !in.mu[k]) return fail(MMOT_ERR_INVALID_ARG, "instance %d: x[%d] or mu[%d] is NULL", q, k, k);
+            T += in.N[k];
+            N[k] += in.N[k];
+        }
     }
     if (T >= (int64_t)1 << 31) return fail(MMOT_ERR_RANGE, "sum N = %lld too large", (long long)T);
+    const double eps = ins[0].eps;
 
-    // ---- inputs to host, validation -------------------------------------
-    std::vector<std::vector<double>> hx(l), hmu(l);
-    for (int k = 0; k < l; ++k) {
-        hx[k].resize(N[k]);
-        hmu[k].resize(N[k]);
-        const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-        CUDA_TRY(cudaMemcpy(hx[k].data(), x[k], sizeof(double) * N[k], kind));
-        CUDA_TRY(cudaMemcpy(hmu[k].data(), mu[k], sizeof(double) * N[k], kind));
-        for (int64_t i = 0; i < N[k]; ++i) {
-            if (!std::isfinite(hx[k][i])) return fail(MMOT_ERR_INVALID_ARG, "x[%d][%lld] not finite", k, (long long)i);
-            if (i > 0 && hx[k][i] < hx[k][i - 1])
-                return fail(MMOT_ERR_UNSORTED, "x[%d] decreases at index %lld", k, (long long)i);
+    // ---- inputs to host, validation, per-instance layouts (layout.h) --------
+    const bool fp64 = (prec == MMOT_FP64);
+    int K = 0, NT = 0, jcap = 0;
+    shape_of(l - 1, fp64, &K, &NT, &jcap);
+    if (tile_points > 0) K = std::max(32, std::min(K, tile_points));
+    const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
+    HostLayout L;
+    L.l = l;
+    std::vector<std::vector<double>> hmu(l);
+    std::vector<int32_t> hseg;
+    std::vector<double> hteps;
+    std::vector<int32_t> seg_tile0(1, 0);
+    std::vector<int64_t> seg_off((size_t)(nin + 1) * l, 0);   // first local index of instance q in marginal k
+    for (int q = 0; q < nin; ++q) {
+        const InstanceIn &in = ins[q];
+        std::vector<std::vector<double>> hx(l), qmu(l);
+        for (int k = 0; k < l; ++k) {
+            const int64_t n = in.N[k];
+            hx[k].resize(n);
+            qmu[k].resize(n);
+            const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+            CUDA_TRY(cudaMemcpy(hx[k].data(), in.x[k], sizeof(double) * n, kind));
+            CUDA_TRY(cudaMemcpy(qmu[k].data(), in.mu[k], sizeof(double) * n, kind));
+            for (int64_t i = 0; i < n; ++i) {
+                if (!std::isfinite(hx[k][i]))
+                    return fail(MMOT_ERR_INVALID_ARG, "instance %d: x[%d][%lld] not finite", q, k, (long long)i);
+                if (i > 0 && hx[k][i] < hx[k][i - 1])
+                    return fail(MMOT_ERR_UNSORTED, "instance %d: x[%d] decreases at index %lld", q, k, (long long)i);
+            }
+            long double sum = 0.0L;
+            for (int64_t i = 0; i < n; ++i) {
+                const double m = qmu[k][i];
+                if (!(m >= 0.0) || !std::isfinite(m))
+                    return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d][%lld] negative or not finite", q, k,
+                                (long long)i);
+                sum += m;
+            }
+            if (std::fabs((double)sum - 1.0) > 1e-9)
+                return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, (double)sum);
+            hmu[k].insert(hmu[k].end(), qmu[k].begin(), qmu[k].end());
+            seg_off[(size_t)(q + 1) * l + k] = seg_off[(size_t)q * l + k] + n;
         }
-        long double s = 0.0L;
-        for (int64_t i = 0; i < N[k]; ++i) {
-            const double m = hmu[k][i];
-            if (!(m >= 0.0) || !std::isfinite(m))
-                return fail(MMOT_ERR_INVALID_ARG, "mu[%d][%lld] negative or not finite", k, (long long)i);
-            s += m;
+        HostLayout Lq;
+        build_layout(l, in.N, hx, in.eps, K, jcap, limit, Lq);
+        append_layout(L, Lq, &seg_off[(size_t)q * l]);
+        for (int b = 0; b < Lq.nt; ++b) {
+            hseg.push_back(q);
+            hteps.push_back(in.eps);
         }
-        if (std::fabs((double)s - 1.0) > 1e-9)
-            return fail(MMOT_ERR_INVALID_ARG, "mu[%d] sums to %.17g, not 1", k, (double)s);
+        seg_tile0.push_back(L.nt);
     }
 
     mmot_plan p = new (std::nothrow) mmot_plan_s();
@@ -641,9 +718,16 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     for (int k = 0; k < l; ++k) p->N[k] = N[k];
     p->NB = l - 1;
     p->NS = 1 << p->NB;
-    const bool fp64 = (prec == MMOT_FP64);
-    int jcap = 0;
-    shape_of(p->NB, fp64, &p->K, &p->NT, &jcap);
+    p->K = K;
+    p->NT = NT;
+    p->nseg = nin;
+    p->batch = batch;
+    p->seg_tile0 = seg_tile0;
+    p->seg_off = seg_off;
+    for (int q = 0; q < nin; ++q) {
+        p->seg_eps.push_back(ins[q].eps);
+        for (int k = 0; k < l; ++k) p->seg_N.push_back(ins[q].N[k]);
+    }
     if (cuda_stream) {
         p->st = (cudaStream_t)cuda_stream;
     } else {
@@ -655,10 +739,7 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
         p->own_stream = true;
     }
 
-    // ---- merged order and tiles (layout.h) ----------------------------------
-    const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
-    HostLayout L;
-    build_layout(l, N, hx, eps, p->K, jcap, limit, L);
+    // ---- merged order and tiles ----------------------------------------------
     const int nt = L.nt;
     p->nt = nt;
     p->h_mid = L.mid;
@@ -669,9 +750,12 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     std::vector<uint32_t> &ts = p->h_tstart;
     std::vector<double> &hspan = L.span, &hpos = L.pos;
     std::vector<int32_t> &hcnt = L.cnt, &href = p->h_reftile;
-    p->h_beta.assign((size_t)nt * l, 0.0);
+    // initial baselines: g_k = -eps ln N_k of the tile's instance
+    p->h_beta0.assign((size_t)nt * l, 0.0);
     for (int b = 0; b < nt; ++b)
-        for (int k = 0; k < l; ++k) p->h_beta[(size_t)b * l + k] = -std::log((double)N[k]);
+        for (int k = 0; k < l; ++k)
+            p->h_beta0[(size_t)b * l + k] = -std::log((double)ins[hseg[b]].N[k]);
+    p->h_beta = p->h_beta0;
 
     // ---- device allocation and upload -------------------------------------
 #define PA(ptr, n)                                          \
@@ -725,6 +809,15 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     PA(p->err, 1);
     PA(p->dsum, 8);
     PA(p->scratch, maxN);
+    if (batch) {
+        PA(p->d_seg, nt);
+        PA(p->d_teps, nt);
+        PA(p->d_frozen, nin);
+        PA(p->d_segt0, nin + 1);
+        PA(p->d_res, nin);
+        PA(p->d_goff, (size_t)(nin + 1) * l);
+        PA(p->d_g0, (size_t)nin * l);
+    }
 #undef PA
 
     auto up = [&](void *d, const void *h, size_t bytes) {
@@ -747,9 +840,10 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     ce = ce ? ce : up(p->urb, hurb.data(), sizeof(double) * nt);
     // exp(-w_s d) from each tile base to the next base in processing order
     std::vector<unsigned char> hdecF, hdecB;
-    if (l <= kMaxOpBits) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB);
+    const std::vector<int32_t> segv = batch ? hseg : std::vector<int32_t>();
+    if (l <= kMaxOpBits) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB, segv);
     if (p->three_phase) {
-        decay_tables(L, p->NB, fp64, hdecF, hdecB);
+        decay_tables(L, p->NB, fp64, hdecF, hdecB, segv);
         ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
         ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());
     }
@@ -759,12 +853,27 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     ce = ce ? ce : up(p->beta, p->h_beta.data(), sizeof(double) * nt * l);
     std::vector<std::vector<double>> hg(l), hlm(l);
     for (int k = 0; k < l && ce == cudaSuccess; ++k) {
-        hg[k].assign(N[k], -eps * std::log((double)N[k]));
+        hg[k].resize(N[k]);
+        for (int q = 0; q < nin; ++q) {
+            const double g0 = -ins[q].eps * std::log((double)ins[q].N[k]);
+            for (int64_t i = seg_off[(size_t)q * l + k]; i < seg_off[(size_t)(q + 1) * l + k]; ++i) hg[k][i] = g0;
+        }
         hlm[k].resize(N[k]);
         for (int64_t i = 0; i < N[k]; ++i) hlm[k][i] = hmu[k][i] > 0 ? std::log(hmu[k][i]) : -INFINITY;
         ce = up(p->g[k], hg[k].data(), sizeof(double) * N[k]);
         ce = ce ? ce : up(p->lnmu[k], hlm[k].data(), sizeof(double) * N[k]);
         ce = ce ? ce : up(p->mu[k], hmu[k].data(), sizeof(double) * N[k]);
+    }
+    if (batch) {
+        std::vector<double> g0((size_t)nin * l);
+        for (int q = 0; q < nin; ++q)
+            for (int k = 0; k < l; ++k) g0[(size_t)q * l + k] = -ins[q].eps * std::log((double)ins[q].N[k]);
+        ce = ce ? ce : up(p->d_seg, hseg.data(), sizeof(int32_t) * nt);
+        ce = ce ? ce : up(p->d_teps, hteps.data(), sizeof(double) * nt);
+        ce = ce ? ce : up(p->d_segt0, seg_tile0.data(), sizeof(int32_t) * (nin + 1));
+        ce = ce ? ce : up(p->d_goff, seg_off.data(), sizeof(int64_t) * seg_off.size());
+        ce = ce ? ce : up(p->d_g0, g0.data(), sizeof(double) * g0.size());
+        ce = ce ? ce : cudaMemsetAsync(p->d_frozen, 0, sizeof(int32_t) * nin, p->st);
     }
     ce = ce ? ce : cudaMemsetAsync(p->err, 0, sizeof(int), p->st);
     ce = ce ? ce : cudaStreamSynchronize(p->st);
@@ -774,6 +883,94 @@ mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, co
     }
     *out = p;
     return MMOT_OK;
+}
+
+// Objective terms of every instance of a plan (one for a single problem):
+// residual over all l marginals, W, primal, dual and mass (Eq. k-mmot
+// distance), from one plan-marginal product per marginal and the objective
+// sweeps.
+mmot_status plan_objective(mmot_plan p, std::vector<mmot_result> &R)
+{
+    const int l = p->l, ns = p->nseg;
+    R.assign(ns, mmot_result{});
+    std::vector<double> Z(ns, 0.0), P(ns, 0.0), D(ns, 0.0), res(ns, 0.0);
+    for (int k = 0; k < l; ++k) {
+        std::vector<double> marg(p->N[k]), g(p->N[k]), m(p->N[k]);
+        mmot_status s = mmot_marginal(p, k, 1, marg.data());
+        if (s != MMOT_OK) return s;
+        CUDA_TRY(cudaMemcpy(g.data(), p->g[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(m.data(), p->mu[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
+        for (int q = 0; q < ns; ++q) {
+            double z = 0.0;
+            for (int64_t i = p->seg_off[(size_t)q * l + k]; i < p->seg_off[(size_t)(q + 1) * l + k]; ++i) {
+                z += marg[i];
+                res[q] += std::fabs(marg[i] - m[i]);
+                if (std::isfinite(g[i])) {
+                    P[q] += g[i] * marg[i];
+                    D[q] += g[i] * m[i];
+                }
+            }
+            if (k == l - 1) Z[q] = z;
+        }
+    }
+    for (int q = 0; q < ns; ++q) {
+        const double e = p->seg_eps[q];
+        R[q].residual = res[q];
+        R[q].mass = Z[q];
+        R[q].primal = P[q];
+        R[q].dual = D[q] + e - e * Z[q];
+        R[q].W = NAN;
+    }
+    if (l > kMaxObjectiveL) return check_device_error(p);
+    // transport cost: per instance, Z times the sum over its tiles of eps W_b / Z_b
+    mmot_status sc = enqueue_cost(p);
+    if (sc != MMOT_OK) return sc;
+    std::vector<double> part(p->nt), lnz(p->nt);
+    CUDA_TRY(cudaMemcpyAsync(part.data(), p->partial, sizeof(double) * p->nt, cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaMemcpyAsync(lnz.data(), p->o_lnz, sizeof(double) * p->nt, cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    for (int q = 0; q < ns; ++q) {
+        double sum = 0.0, c = 0.0;
+        for (int b = p->seg_tile0[q]; b < p->seg_tile0[q + 1]; ++b) {
+            const double y = part[b] - c;
+            const double t = sum + y;
+            c = (t - sum) - y;
+            sum = t;
+        }
+        const double lz = lnz[p->seg_tile0[q]];
+        R[q].W = (lz == -INFINITY) ? 0.0 : sum * std::exp(lz);
+    }
+    return check_device_error(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mmot_last_error(void) { return g_last_error.c_str(); }
+
+void mmot_destroy(mmot_plan p)
+{
+    if (!p) return;
+    if (p->st) cudaStreamSynchronize(p->st);
+    delete p;
+}
+
+mmot_status mmot_plan_create(int l, const int64_t *N, const double *const *x, const double *const *mu,
+                             double eps, mmot_precision prec, int inputs_on_device, void *cuda_stream,
+                             mmot_plan *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(MMOT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (l < 2 || l > MMOT_MAXL) return fail(MMOT_ERR_INVALID_ARG, "l = %d outside [2, 8]", l);
+    if (!N || !x || !mu) return fail(MMOT_ERR_INVALID_ARG, "N, x or mu is NULL");
+    std::vector<InstanceIn> ins(1);
+    ins[0].N = N;
+    ins[0].x = x;
+    ins[0].mu = mu;
+    ins[0].eps = eps;
+    return plan_build(l, ins, prec, inputs_on_device, cuda_stream, out);
 }
 
 mmot_status mmot_marginal(mmot_plan p, int k, int plan_marginal, double *out)
@@ -844,41 +1041,11 @@ mmot_status mmot_objective(mmot_plan p, mmot_result *out)
 {
     if (!p || !out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or out");
     memset(out, 0, sizeof(*out));
-    // marginals of the plan, one product per marginal
-    double P = 0.0, D = 0.0, Z = 0.0, res = 0.0;
-    for (int k = 0; k < p->l; ++k) {
-        std::vector<double> marg(p->N[k]), g(p->N[k]), m(p->N[k]);
-        mmot_status s = mmot_marginal(p, k, 1, marg.data());
-        if (s != MMOT_OK) return s;
-        CUDA_TRY(cudaMemcpy(g.data(), p->g[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
-        CUDA_TRY(cudaMemcpy(m.data(), p->mu[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
-        double z = 0.0;
-        for (int64_t i = 0; i < p->N[k]; ++i) {
-            z += marg[i];
-            res += std::fabs(marg[i] - m[i]);
-            if (std::isfinite(g[i])) {
-                P += g[i] * marg[i];
-                D += g[i] * m[i];
-            }
-        }
-        if (k == p->l - 1) Z = z;
-    }
-    out->iters = 0;
-    out->residual = res;
-    out->mass = Z;
-    out->primal = P;
-    out->dual = D + p->eps - p->eps * Z;
-    out->W = NAN;
-    if (p->l > kMaxObjectiveL) return check_device_error(p);
-    // transport cost: sum over tiles of eps W_b / Z_b, times Z
-    mmot_status sc = enqueue_cost(p);
-    if (sc != MMOT_OK) return sc;
-    double wz = 0.0, lnz = 0.0;
-    CUDA_TRY(cudaMemcpyAsync(&wz, p->dsum, sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    CUDA_TRY(cudaMemcpyAsync(&lnz, p->o_lnz, sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    CUDA_TRY(cudaStreamSynchronize(p->st));
-    out->W = (lnz == -INFINITY) ? 0.0 : wz * std::exp(lnz);
-    return check_device_error(p);
+    std::vector<mmot_result> R;
+    mmot_status s = plan_objective(p, R);
+    if (s != MMOT_OK) return s;
+    *out = R[0];
+    return MMOT_OK;
 }
 
 mmot_status mmot_solve(mmot_plan p, double tol, int itr_max, mmot_result *out)
@@ -964,12 +1131,15 @@ mmot_status mmot_reset_potentials(mmot_plan p)
     if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
     const int l = p->l;
     for (int k = 0; k < l; ++k) {
-        k_reset<<<64, 256, 0, p->st>>>(p->g[k], p->N[k], -p->eps * std::log((double)p->N[k]));
+        if (p->batch)
+            k_reset_seg<<<p->nseg, 256, 0, p->st>>>(p->g[k], p->d_goff, p->d_g0, k, l);
+        else
+            k_reset<<<64, 256, 0, p->st>>>(p->g[k], p->N[k], -p->eps * std::log((double)p->N[k]));
         CUDA_TRY(cudaGetLastError());
         p->launches += 1;
     }
-    for (int b = 0; b < p->nt; ++b)
-        for (int k = 0; k < l; ++k) p->h_beta[(size_t)b * l + k] = -std::log((double)p->N[k]);
+    if (p->batch) CUDA_TRY(cudaMemsetAsync(p->d_frozen, 0, sizeof(int32_t) * p->nseg, p->st));
+    p->h_beta = p->h_beta0;
     CUDA_TRY(cudaMemcpyAsync(p->beta, p->h_beta.data(), sizeof(double) * p->h_beta.size(),
                              cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaMemsetAsync(p->lphi, 0, (size_t)p->T * p->esz, p->st));
@@ -1013,6 +1183,267 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
     info->precision = p->prec;
     info->kernel_launches = p->launches;
     return MMOT_OK;
+}
+
+// ---- batches ------------------------------------------------------------------
+
+}  // extern "C"
+
+struct mmot_batch_s {
+    int n = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    struct Group {
+        int l = 0;
+        mmot_plan p = nullptr;
+        std::vector<int> inst;        // batch index of each instance of the group
+        std::vector<int> iters;       // iterations when found converged (else run so far)
+        std::vector<double> res;      // last checked residual
+        std::vector<int32_t> conv;    // converged (frozen)
+        int done = 0;                 // iterations run on the group
+        int active = 0;
+    };
+    std::vector<Group> groups;
+    std::vector<std::pair<int, int>> where;   // instance -> (group, index in group)
+    ~mmot_batch_s()
+    {
+        for (auto &g : groups) mmot_destroy(g.p);
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+};
+
+namespace {
+
+// per-instance residual of marginals 1..l-1 of a group; freeze the converged
+mmot_status group_check(mmot_batch_s::Group &G, double tol)
+{
+    mmot_plan p = G.p;
+    const int ns = p->nseg;
+    CUDA_TRY(cudaMemsetAsync(p->d_res, 0, sizeof(double) * ns, p->st));
+    for (int k = 0; k < p->l - 1; ++k) {
+        mmot_status s = enqueue_product(p, k, MODE_RESIDUAL, nullptr);
+        if (s != MMOT_OK) return s;
+        k_seg_sum<<<(ns + 127) / 128, 128, 0, p->st>>>(p->partial, p->d_segt0, ns, p->d_res, 1);
+        CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
+    }
+    std::vector<double> r(ns);
+    CUDA_TRY(cudaMemcpyAsync(r.data(), p->d_res, sizeof(double) * ns, cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    int active = 0;
+    bool changed = false;
+    for (int q = 0; q < ns; ++q) {
+        if (G.conv[q]) continue;
+        G.res[q] = r[q];
+        G.iters[q] = G.done;
+        if (r[q] <= tol) {
+            G.conv[q] = 1;
+            changed = true;
+        } else {
+            ++active;
+        }
+    }
+    G.active = active;
+    if (changed)
+        CUDA_TRY(cudaMemcpyAsync(p->d_frozen, G.conv.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, p->st));
+    return check_device_error(p);
+}
+
+mmot_status group_reset(mmot_batch_s::Group &G)
+{
+    mmot_status s = mmot_reset_potentials(G.p);
+    if (s != MMOT_OK) return s;
+    const int ns = (int)G.inst.size();
+    G.iters.assign(ns, 0);
+    G.res.assign(ns, INFINITY);
+    G.conv.assign(ns, 0);
+    G.done = 0;
+    G.active = ns;
+    return MMOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mmot_status mmot_batch_create(int n, const int *l, const int64_t *N, const double *const *x,
+                              const double *const *mu, const double *eps, mmot_precision prec,
+                              int tile_points, void *cuda_stream, mmot_batch *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(MMOT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !l || !N || !x || !mu || !eps) return fail(MMOT_ERR_INVALID_ARG, "n < 1 or NULL argument");
+    if (tile_points < 0) return fail(MMOT_ERR_INVALID_ARG, "tile_points < 0");
+    std::vector<int64_t> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        if (l[i] < 2 || l[i] > MMOT_MAXL) return fail(MMOT_ERR_INVALID_ARG, "instance %d: l = %d outside [2, 8]", i, l[i]);
+        off[i + 1] = off[i] + l[i];
+    }
+    mmot_batch b = new (std::nothrow) mmot_batch_s();
+    if (!b) return fail(MMOT_ERR_OOM, "host allocation failed");
+    b->n = n;
+    if (cuda_stream) {
+        b->st = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return fail(MMOT_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
+        }
+        b->own_stream = true;
+    }
+    b->where.assign(n, {-1, -1});
+    for (int L = 2; L <= MMOT_MAXL; ++L) {
+        std::vector<InstanceIn> ins;
+        std::vector<int> idx;
+        for (int i = 0; i < n; ++i) {
+            if (l[i] != L) continue;
+            InstanceIn in;
+            in.N = N + off[i];
+            in.x = x + off[i];
+            in.mu = mu + off[i];
+            in.eps = eps[i];
+            ins.push_back(in);
+            idx.push_back(i);
+        }
+        if (ins.empty()) continue;
+        mmot_batch_s::Group G;
+        G.l = L;
+        mmot_status s = plan_build(L, ins, prec, 0, b->st, &G.p, tile_points, true);
+        if (s != MMOT_OK) {
+            // report the batch index of a failing instance
+            std::string m = g_last_error;
+            delete b;
+            return fail(s, "l = %d group: %s", L, m.c_str());
+        }
+        G.inst = idx;
+        for (size_t q = 0; q < idx.size(); ++q) b->where[idx[q]] = {(int)b->groups.size(), (int)q};
+        b->groups.push_back(G);
+        s = group_reset(b->groups.back());
+        if (s != MMOT_OK) {
+            delete b;
+            return s;
+        }
+    }
+    *out = b;
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_reset(mmot_batch b)
+{
+    if (!b) return fail(MMOT_ERR_INVALID_ARG, "NULL batch");
+    for (auto &G : b->groups) {
+        mmot_status s = group_reset(G);
+        if (s != MMOT_OK) return s;
+    }
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_step(mmot_batch b, int n_iters, double tol, int *active_out)
+{
+    if (!b) return fail(MMOT_ERR_INVALID_ARG, "NULL batch");
+    if (n_iters < 0) return fail(MMOT_ERR_INVALID_ARG, "n_iters < 0");
+    int active = 0;
+    for (auto &G : b->groups) {
+        if (G.active == 0) continue;
+        mmot_status s = mmot_sinkhorn_step(G.p, n_iters, nullptr);
+        if (s != MMOT_OK) return s;
+        G.done += n_iters;
+        s = group_check(G, tol);
+        if (s != MMOT_OK) return s;
+        active += G.active;
+    }
+    if (active_out) *active_out = active;
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_solve(mmot_batch b, double tol, int itr_max, int check_every, mmot_result *results)
+{
+    if (!b) return fail(MMOT_ERR_INVALID_ARG, "NULL batch");
+    if (itr_max < 0 || check_every < 1) return fail(MMOT_ERR_INVALID_ARG, "itr_max < 0 or check_every < 1");
+    mmot_status s = mmot_batch_reset(b);
+    if (s != MMOT_OK) return s;
+    int t = 0, active = b->n;
+    while (t < itr_max && active > 0) {
+        const int n = std::min(check_every, itr_max - t);
+        s = mmot_batch_step(b, n, tol, &active);
+        if (s != MMOT_OK) return s;
+        t += n;
+    }
+    if (itr_max == 0) {
+        for (auto &G : b->groups) {
+            s = group_check(G, tol);
+            if (s != MMOT_OK) return s;
+        }
+    }
+    if (results) {
+        for (auto &G : b->groups) {
+            std::vector<mmot_result> R;
+            s = plan_objective(G.p, R);
+            if (s != MMOT_OK) return s;
+            for (size_t q = 0; q < G.inst.size(); ++q) {
+                mmot_result r = R[q];
+                r.iters = G.iters[q];
+                r.residual = G.res[q];
+                results[G.inst[q]] = r;
+            }
+        }
+    }
+    for (auto &G : b->groups)
+        if (G.active > 0) return fail(MMOT_ERR_NOT_CONVERGED, "%d instance(s) with l = %d above tol after %d iterations",
+                                      G.active, G.l, t);
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_status(mmot_batch b, int i, int *iters, double *residual, int *converged)
+{
+    if (!b) return fail(MMOT_ERR_INVALID_ARG, "NULL batch");
+    if (i < 0 || i >= b->n) return fail(MMOT_ERR_INVALID_ARG, "instance %d out of range", i);
+    const auto &G = b->groups[b->where[i].first];
+    const int q = b->where[i].second;
+    if (iters) *iters = G.iters[q];
+    if (residual) *residual = G.res[q];
+    if (converged) *converged = G.conv[q];
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_get_potentials(mmot_batch b, int i, int k, double *g_out)
+{
+    if (!b || !g_out) return fail(MMOT_ERR_INVALID_ARG, "NULL batch or output");
+    if (i < 0 || i >= b->n) return fail(MMOT_ERR_INVALID_ARG, "instance %d out of range", i);
+    const auto &G = b->groups[b->where[i].first];
+    const int q = b->where[i].second;
+    mmot_plan p = G.p;
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    const int64_t o = p->seg_off[(size_t)q * p->l + k];
+    const int64_t n = p->seg_off[(size_t)(q + 1) * p->l + k] - o;
+    CUDA_TRY(cudaMemcpyAsync(g_out, p->g[k] + o, sizeof(double) * n, cudaMemcpyDefault, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_get_info(mmot_batch b, mmot_batch_info *info)
+{
+    if (!b || !info) return fail(MMOT_ERR_INVALID_ARG, "NULL batch or info");
+    info->instances = b->n;
+    info->groups = (int)b->groups.size();
+    info->total_points = 0;
+    info->tiles = 0;
+    info->kernel_launches = 0;
+    for (auto &G : b->groups) {
+        info->total_points += G.p->T;
+        info->tiles += G.p->nt;
+        info->kernel_launches += G.p->launches;
+    }
+    return MMOT_OK;
+}
+
+void mmot_batch_destroy(mmot_batch b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    delete b;
 }
 
 }  // extern "C"

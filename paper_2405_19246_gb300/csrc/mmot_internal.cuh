@@ -87,7 +87,15 @@ struct SweepArgs {
     double *out;              // [N_j] output for the OUT modes
     double *partial;          // [nt] per-tile residual sums
     int *err;                 // error bits
+    // batches of independent instances (all NULL for a single instance):
+    // tiles never straddle two instances and no state crosses a boundary
+    const int32_t *seg;       // [nt] instance of each tile (nondecreasing)
+    const double *teps;       // [nt] eps of each tile's instance
+    const int32_t *frozen;    // [instances] nonzero: updates and residual terms skipped
 };
+
+// eps of tile b
+__host__ __device__ inline double tile_eps(const SweepArgs &a, int b) { return a.teps ? a.teps[b] : a.eps; }
 
 // Host-side launchers (one per bit count NB = l-1, instantiated per precision).
 // Look-back design (every l): k_bwd then k_fwd.

@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(NT) k_objective(SweepArgs a)
         for (int s = 0; s <= NB; ++s) s_ev[s] = (V)fmax(d[s] - gmx, -1.0e30);
     }
     __syncthreads();
-    const V gap0 = (b > 0) ? (V)(a.ulb[b] - a.urb[b - 1]) : V(0);
+    // gap before the tile's first point (none at the start of an instance)
+    const bool first = (b == 0) || (a.seg && a.seg[b - 1] != a.seg[b]);
+    const V gap0 = first ? V(0) : (V)(a.ulb[b] - a.urb[b - 1]);
     Sf<V> accW = sf_zero<V>(), accZ = sf_zero<V>();
     e.template walk_each<true>([&](int c) {
         const int id = e.idx[c];
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_objective(SweepArgs a)
             a.out[b] = -INFINITY;
         } else {
             const double r = (tot.m == V(0)) ? 0.0 : ldexp((double)tot.m / (double)accZ.m, tot.k - accZ.k);
-            a.partial[b] = a.eps * r;
+            a.partial[b] = tile_eps(a, b) * r;
             a.out[b] = log((double)accZ.m) + (double)accZ.k * kLn2 + s_base;
         }
     }

@@ -555,10 +555,13 @@ struct Engine {
         Sf<V> part[NL];
 #pragma unroll
         for (int S = 0; S < NL; ++S) part[S] = sf_zero<V>();
+        const int myseg = a.seg ? a.seg[b] : 0;
         int base = v - 1;
         while (base >= 0) {
             const int p = base - lane;
-            int f = (p >= 0) ? ld_acquire(a.flags + (size_t)p * (NB + 1) + s) : 2;
+            // a predecessor of another instance contributes nothing and ends the window
+            const bool other = (p >= 0) && a.seg && a.seg[fwd ? p : a.nt - 1 - p] != myseg;
+            int f = (p >= 0 && !other) ? ld_acquire(a.flags + (size_t)p * (NB + 1) + s) : 2;
             unsigned incl;
             int it = 0;
             while (true) {
@@ -579,7 +582,7 @@ struct Engine {
                 fail = true;
                 break;
             }
-            if (lane <= first && p >= 0) {
+            if (lane <= first && p >= 0 && !other) {
                 const int bp = fwd ? p : a.nt - 1 - p;
                 const double d = fwd ? (ub - a.ulb[bp]) : (a.urb[bp] - ub);
                 // decay exp(-w_s d) as (fraction, integer) of a power of two
@@ -807,6 +810,16 @@ __device__ void load_tile(SweepSmem<NB, V, NT, C, JCAP, WITH_G> &sm, const Sweep
     __syncthreads();
 }
 
+// Tiles of a frozen (converged) instance of a batch do no update or residual
+// work; their residual term is 0.
+__device__ __forceinline__ bool skip_tile(const SweepArgs &a, int b)
+{
+    if (!a.frozen || (a.mode != MODE_UPDATE && a.mode != MODE_RESIDUAL)) return false;
+    if (!a.frozen[a.seg[b]]) return false;
+    if (a.mode == MODE_RESIDUAL && threadIdx.x == 0) a.partial[b] = 0.0;
+    return true;
+}
+
 template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 __global__ void __launch_bounds__(NT, 3) k_bwd(SweepArgs a)
 {
@@ -821,6 +834,7 @@ __global__ void __launch_bounds__(NT, 3) k_bwd(SweepArgs a)
     const int v = s_v;
     if (v >= a.nt) return;
     const int b = a.nt - 1 - v;
+    if (skip_tile(a, b)) return;
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
     load_tile<NB, V, NT, C, JCAP, false>(sm, a, b, n, t0, a.j);
@@ -846,6 +860,8 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
     const V span = (V)a.span[b];
+    const double eps_b = tile_eps(a, b);
+    const double inv_eps_b = a.teps ? 1.0 / eps_b : a.inv_eps;
     load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
 
     // ranks of the target points (forward order)
@@ -1014,7 +1030,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
         for (int c = 0; c < C; ++c) {
             if (e.bit[c] == -1) {
                 const int i = off + sm.slot[e.idx[c]];
-                a.gj[i] = a.eps * gq[c];
+                a.gj[i] = eps_b * gq[c];
                 const V lp = (V)(gq[c] - bnew);
                 static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
                 sm.lphi[e.idx[c]] = lp;
@@ -1028,7 +1044,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
                 const int i = off + sm.slot[e.idx[c]];
                 const double gg = a.gj[i];
                 const double marg = (gg == -INFINITY || xM[c] == V(-INFINITY))
-                                        ? 0.0 : exp_acc<V>(gg * a.inv_eps + (base + (double)xM[c]));
+                                        ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)xM[c]));
                 acc += fabs(marg - a.muj[i]);
             }
         }
@@ -1051,7 +1067,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
                 if (a.mode == MODE_OUT_M)
                     r = exp_acc<V>(lnMc);
                 else if (a.mode == MODE_OUT_PLAN)
-                    r = (a.gj[i] == -INFINITY) ? 0.0 : exp_acc<V>(a.gj[i] * a.inv_eps + lnMc);
+                    r = (a.gj[i] == -INFINITY) ? 0.0 : exp_acc<V>(a.gj[i] * inv_eps_b + lnMc);
                 else
                     r = lnMc;
                 a.out[i] = r;
@@ -1072,6 +1088,7 @@ __global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
     __syncthreads();
     const int v = s_v;
     if (v >= a.nt) return;
+    if (skip_tile(a, v)) return;
     product_body<NB, V, NT, C, JCAP, true>(sm, a, v, v);
 }
 
@@ -1148,10 +1165,17 @@ __device__ void tile_operator(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swe
     __syncthreads();
     // absolute scaled floats with the decay to the next base
     double d = 0.0;
+    bool cut = false;   // the next tile belongs to another instance of a batch
     if (fwd) {
-        if (b + 1 < a.nt) d = a.ulb[b + 1] - a.ulb[b];
+        if (b + 1 < a.nt) {
+            d = a.ulb[b + 1] - a.ulb[b];
+            cut = a.seg && a.seg[b + 1] != a.seg[b];
+        }
     } else {
-        if (b >= 1) d = a.urb[b] - a.urb[b - 1];
+        if (b >= 1) {
+            d = a.urb[b] - a.urb[b - 1];
+            cut = a.seg && a.seg[b - 1] != a.seg[b];
+        }
     }
     SfT<V> *dst = sfp<V>(fwd ? a.opF : a.opB) + (size_t)b * NB * NS;
     for (int idx = tid; idx < NB * NS; idx += NT) {
@@ -1167,7 +1191,7 @@ __device__ void tile_operator(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swe
             if ((U >> k) & 1) bu += sm.beta[k];
         const double wsu = (double)su * (double)(L - su);
         const V val = scr[s * NS + U];
-        dst[idx] = sf_store(sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d));
+        dst[idx] = cut ? sf_store(sf_zero<V>()) : sf_store(sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d));
     }
     __syncthreads();
 }
@@ -1193,6 +1217,7 @@ __global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
     const int b = blockIdx.x;
+    if (skip_tile(a, b)) return;
     product_body<NB, V, NT, C, JCAP, false>(sm, a, b, b);
     if (a.jnext >= 0) {
         // operators of the next target from the updated potentials of this tile
@@ -1385,7 +1410,9 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
             Sf<V> part[NS];
 #pragma unroll
             for (int T = 0; T < NS; ++T) part[T] = sf_zero<V>();
-            if (lane < c) {
+            // chunk p's contribution reaches this chunk only inside one instance
+            const bool same = !a.seg || a.seg[tile_of(min(nt - 1, (lane + 1) * Rc))] == a.seg[tile_of(min(nt - 1, c * Rc))];
+            if (lane < c && same) {
                 const int p = lane;
                 const int f = wait_flag(cflag + (size_t)p * (NB + 1) + s, a.err, a.spin_limit);
                 if (f < 0) {

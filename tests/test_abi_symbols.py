@@ -49,3 +49,20 @@ def test_last_error_without_gpu():
     assert st == 1
     assert b"l = 1" in L.mmot_last_error()
     L.mmot_destroy(None)
+
+
+def test_batch_rejects_bad_arguments_without_gpu():
+    from paper_2405_19246_gb300 import _build, _native
+    _build.build()
+    L = _native.lib()
+    h = ctypes.c_void_p()
+    assert L.mmot_batch_create(0, None, None, None, None, None, 1, 0, None, ctypes.byref(h)) == 1
+    ls = (ctypes.c_int * 2)(3, 9)
+    N = (ctypes.c_int64 * 12)(*([4] * 12))
+    X = (ctypes.c_void_p * 12)()
+    eps = (ctypes.c_double * 2)(0.1, 0.1)
+    st = L.mmot_batch_create(2, ls, N, X, X, eps, 1, 0, None, ctypes.byref(h))
+    assert st == 1
+    assert b"instance 1: l = 9" in L.mmot_last_error()
+    assert L.mmot_batch_create(2, ls, N, X, X, eps, 1, -1, None, ctypes.byref(h)) == 1
+    L.mmot_batch_destroy(None)

@@ -1,0 +1,127 @@
+"""GPU parity of batches of independent instances.
+
+A batch lays instances with the same l out one after another; no state may
+cross an instance boundary and every instance keeps its own eps.  Each
+instance of a batch must therefore give what the same instance gives alone
+(a single-instance plan, same iteration count), within the FP32 / FP64
+tolerances, and what the oracle gives.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_19246_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2405_19246_gb300 import api as A
+    return A
+
+
+def _mixed_instances(count, seed, N_range=(40, 900), eps_range=(5e-3, 1e-1), l_range=(2, 8)):
+    params = wl.batched_instance_params(count, seed_cfg=seed, l_range=l_range, N_range=N_range,
+                                        eps_range=eps_range)
+    inst = []
+    for i, (l, N, eps) in enumerate(params):
+        xs, mus = wl.batched_instance(i, l, int(N), seed_cfg=seed)
+        inst.append((xs, mus, eps))
+    return inst
+
+
+TOL_G = {"fp32": 2e-4, "fp64": 1e-9}   # potentials after a few iterations, in units of eps
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_iterations_match_single_instances(api, prec):
+    inst = _mixed_instances(24, seed=901)
+    n_it = 4
+    with api.Batch(inst, precision=prec) as B:
+        assert B.info()["groups"] >= 5
+        B.step(n_it, 0.0)
+        for i, (xs, mus, eps) in enumerate(inst):
+            with api.Plan(xs, mus, eps, precision=prec) as P:
+                P.sinkhorn_step(n_it)
+                for k in range(len(xs)):
+                    d = np.max(np.abs(B.get_potentials(i, k) - P.get_potentials(k))) / eps
+                    assert d <= TOL_G[prec], (i, k, d)
+
+
+def test_batch_matches_oracle(api):
+    inst = _mixed_instances(10, seed=902, N_range=(30, 300), l_range=(2, 5))
+    n_it = 3
+    with api.Batch(inst, precision="fp64") as B:
+        B.step(n_it, 0.0)
+        for i, (xs, mus, eps) in enumerate(inst):
+            gs = [np.full(len(x), -eps * math.log(len(x))) for x in xs]
+            for _ in range(n_it):
+                for j in range(len(xs)):
+                    gs[j] = oracle.potential_update(mus[j], oracle.marginal_subset(xs, gs, eps, j), eps)
+            for k in range(len(xs)):
+                d = np.max(np.abs(B.get_potentials(i, k) - gs[k])) / eps
+                assert d <= 1e-9, (i, k, d)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_solve_stops_each_instance(api, prec):
+    """Each instance stops at the first check with residual <= tol; its result
+    equals the same instance run alone for the same number of iterations."""
+    inst = _mixed_instances(16, seed=903, N_range=(40, 400), eps_range=(3e-2, 1e-1), l_range=(2, 6))
+    tol = 1e-6 if prec == "fp64" else 1e-5
+    with api.Batch(inst, precision=prec) as B:
+        res = B.solve(tol, 3000, check_every=5)
+        iters = [r["iters"] for r in res]
+        assert len(set(iters)) > 1          # instances stop at different checks
+        for i, (xs, mus, eps) in enumerate(inst):
+            st = B.status(i)
+            assert st["converged"] and st["residual"] <= tol, (i, st)
+            assert iters[i] % 5 == 0
+            with api.Plan(xs, mus, eps, precision=prec) as P:
+                out = P.solve(0.0, iters[i])
+                for k in range(len(xs)):
+                    d = np.max(np.abs(B.get_potentials(i, k) - P.get_potentials(k))) / eps
+                    assert d <= 50 * TOL_G[prec], (i, k, d)
+                if len(xs) < 8:
+                    assert abs(res[i]["W"] - out["W"]) <= 1e-4 * abs(out["W"]), (i, res[i]["W"], out["W"])
+                assert abs(res[i]["mass"] - out["mass"]) <= 1e-5
+
+
+def test_frozen_instance_keeps_its_potentials(api):
+    inst = _mixed_instances(8, seed=904, N_range=(40, 300), eps_range=(2e-2, 1e-1), l_range=(3, 6))
+    with api.Batch(inst, precision="fp32") as B:
+        B.step(3, 0.0)
+        r = np.array([B.status(i)["residual"] for i in range(len(inst))])
+        tol = float(np.median(r))
+        B.step(0, tol)       # no iteration: freezes the instances at or below the median
+        frozen = [B.status(i)["converged"] for i in range(len(inst))]
+        assert 0 < sum(frozen) < len(inst)
+        before = [[B.get_potentials(i, k) for k in range(len(inst[i][0]))] for i in range(len(inst))]
+        B.step(4, 0.0)
+        for i in range(len(inst)):
+            for k in range(len(inst[i][0])):
+                g = B.get_potentials(i, k)
+                if frozen[i]:
+                    np.testing.assert_array_equal(g, before[i][k])
+                else:
+                    assert np.max(np.abs(g - before[i][k])) > 0.0
+
+
+def test_instance_result_is_independent_of_its_neighbours(api):
+    """The same instance in two different batches gives the same potentials."""
+    inst = _mixed_instances(12, seed=905, N_range=(40, 600), l_range=(3, 6))
+    other = _mixed_instances(12, seed=906, N_range=(40, 600), l_range=(3, 6))
+    mix = other[:5] + [inst[3]] + other[5:]
+    with api.Batch(inst, precision="fp32") as A, api.Batch(mix, precision="fp32") as B:
+        A.step(6, 0.0)
+        B.step(6, 0.0)
+        xs, mus, eps = inst[3]
+        for k in range(len(xs)):
+            d = np.max(np.abs(A.get_potentials(3, k) - B.get_potentials(5, k))) / eps
+            assert d <= TOL_G["fp32"], (k, d)
