@@ -34,7 +34,6 @@ __global__ void __launch_bounds__(NT) k_objective(SweepArgs a)
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
     __shared__ int s_v;
-    __shared__ V s_ev[NB + 1];
     __shared__ double s_base;
     __shared__ V s_wm[NW];
     __shared__ int s_wk[NW];
@@ -68,7 +67,7 @@ __global__ void __launch_bounds__(NT) k_objective(SweepArgs a)
 #pragma unroll(En::UNR)
         for (int U = 0; U < NS; ++U) sm.G[U * K + id] = (U == 0) ? V(1) : (e.carry[U] + e.run[U]);
     });
-    if (tid <= NB) sm.gamG[tid] = sm.gam[tid];
+    for (int S = tid; S < NS; S += NT) sm.GsG[S] = sm.Gs[S];
     __syncthreads();
 
     // ---- forward states --------------------------------------------------------
@@ -83,52 +82,58 @@ __global__ void __launch_bounds__(NT) k_objective(SweepArgs a)
         __syncthreads();
         e.template all_levels<false>(sm, a, v, b, true);
     }
-    // per-level exponents gamma^F_s + gamma^G_{l-s} - w_s span, relative to
-    // their maximum (FP64), and the tile's FP64 base
+    // binary exponent of the product of the two states' scales, and the FP64
+    // base; the factor exp(-w_s span) is the same at every point of the tile
+    for (int S = tid; S < NS; S += NT) sm.eS[S] = (sm.Gs[S].k - 1) + (sm.GsG[FULLS ^ S].k - 1);
     if (tid == 0) {
-        double d[NB + 1];
-        double gmx = -INFINITY;
-        for (int s = 0; s <= NB; ++s) {
-            d[s] = sm.gam[s] + sm.gamG[NB - s] - (double)En::rate(s) * (double)span;
-            gmx = fmax(gmx, d[s]);
-        }
         double sb = 0.0;
         for (int k = 0; k < NB; ++k) sb += sm.beta[k];
-        s_base = sb + gmx;
-        for (int s = 0; s <= NB; ++s) s_ev[s] = (V)fmax(d[s] - gmx, -1.0e30);
+        s_base = sb;
     }
     __syncthreads();
+    V q[NB + 1];
+#pragma unroll
+    for (int s = 0; s <= NB; ++s) q[s] = vexp<V>(-En::rate(s) * span);
     // gap before the tile's first point (none at the start of an instance)
     const bool first = (b == 0) || (a.seg && a.seg[b - 1] != a.seg[b]);
     const V gap0 = first ? V(0) : (V)(a.ulb[b] - a.urb[b - 1]);
     Sf<V> accW = sf_zero<V>(), accZ = sf_zero<V>();
     e.template walk_each<true>([&](int c) {
         const int id = e.idx[c];
-        V X[NB + 1];
-#pragma unroll
-        for (int s = 0; s <= NB; ++s) X[s] = V(0);
+        // sum over S of w_S F_S G_{S^c} (and without weights for Z), as
+        // mantissa x 2^exponent with a running maximum exponent
+        int Emax = INT_MIN / 2;
+        V sw = V(0), sz = V(0);
 #pragma unroll(En::UNR)
         for (int S = 0; S < NS; ++S) {
             const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
-            X[popc_c(S)] += fS * sm.G[(FULLS ^ S) * K + id];
-        }
-        V emx = V(-INFINITY);
-#pragma unroll
-        for (int s = 0; s <= NB; ++s)
-            if (X[s] > V(0)) emx = (s_ev[s] > emx) ? s_ev[s] : emx;
-        if (!(emx > V(-INFINITY))) return;
-        V sw = V(0), sz = V(0);
-#pragma unroll
-        for (int s = 0; s <= NB; ++s) {
-            if (X[s] > V(0)) {
-                const V t = vexp<V>(s_ev[s] - emx) * X[s];
-                sw = fma(En::rate(s), t, sw);
-                sz += t;
+            const Sf<V> fm = sf_make<V>(fS);
+            const Sf<V> gm = sf_make<V>(sm.G[(FULLS ^ S) * K + id]);
+            if (fm.m != V(0) && gm.m != V(0)) {
+                const int s = popc_c(S);
+                const V z = fm.m * gm.m * q[s];
+                const int E = fm.k + gm.k + sm.eS[S];
+                if (E > Emax) {
+                    const V r = pow2neg<V>(Emax - E);
+                    sw = fma(sw, r, En::rate(s) * z);
+                    sz = fma(sz, r, z);
+                    Emax = E;
+                } else {
+                    const V r = pow2neg<V>(E - Emax);
+                    sw = fma(En::rate(s) * z, r, sw);
+                    sz = fma(z, r, sz);
+                }
             }
         }
+        if (!(sz > V(0))) return;
         const V dx = (id > 0) ? sm.pos[id] - sm.pos[id - 1] : gap0;
-        accW = sf_add(accW, sf_scale_exp(sf_make<V>(dx * sw), (double)emx));
-        if (id == 0) accZ = sf_scale_exp(sf_make<V>(sz), (double)emx);
+        Sf<V> t = sf_make<V>(dx * sw);
+        t.k += Emax;
+        if (t.m != V(0)) accW = sf_add(accW, t);
+        if (id == 0) {
+            accZ = sf_make<V>(sz);
+            accZ.k += Emax;
+        }
     });
     const Sf<V> ws = sf_warp_sum(accW);
     if (lane == 0) {

@@ -35,6 +35,7 @@
 // at the target points, then applies the FP64 epilogue (potential update
 // g_j = eps (ln mu_j - ln M_j), or an output mode).
 #pragma once
+#include <limits>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -310,19 +311,21 @@ struct SweepSmem {
     static constexpr int NW = NT / 32;
     Sf<V> E[NS];           // carry of each state at the tile base (absolute)
     Sf<V> Eh[NS];          // the same times exp(-sum_{m in S} beta_m)
-    Sf<V> Gs[NB + 2];      // exp(gamma_s) of the current pass
-    double gam[NB + 1];    // level scales of the current pass
-    double gamG[NB + 1];   // level scales of the backward pass (k_fwd)
+    Sf<V> Gs[NS];          // scale of each state (provisional while its level runs)
+    Sf<V> GsG[NS];         // final scales of the backward pass (combine)
+    V rr[NS][NB];          // injection ratio into state T at a point of bit k
+    V rhoS[NS];            // provisional-to-final rescale of each state of the level
+    int eS[NS];            // combine: binary exponent of scale(F_S) * scale(G_{R\S})
     double beta[NB];       // baselines of the marginals mapped to bits
     double dred[NW];       // FP64 reduction scratch
     V scan[NW][NS];        // warp totals / warp prefixes
     V tot[NS];             // block totals of the current level
     V tc[NS];              // tile carries in f-representation
-    V rho;                 // rescale factor of the current level
-    V D[NB];               // provisional level scales
+    V D[NB];               // provisional level shifts
     V fred[NW][NB];        // reduction scratch
     int ired[NW];
     int ntarget;
+    int bits;              // bits (marginals other than the target) present in the tile
     V pos[K];
     V lphi[K];
     int16_t slot[K];
@@ -353,9 +356,10 @@ struct Engine {
     int bit[C];     // bit of the point's marginal; -1 target; -2 padding
     int idx[C];     // index within the tile (forward order)
     V pp[C];        // position in the pass frame (units of eps)
-    V fac[C][NB];   // injection factor per level
+    V fac[C][NB];   // injection factor per level (before the per-state ratios)
     V carry[NS];    // thread carries (f-representation), final levels only
     V run[NS];      // running local sums of the current walk
+    const V *rrp;   // the tile's injection ratios (shared memory, [NS][NB])
 
     // rate w_s = s(l - s) with l = NB + 1
     __device__ static constexpr V rate(int s) { return (V)(s * (L - s)); }
@@ -390,11 +394,16 @@ struct Engine {
 
             }
         }
+        int msk = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            if (bit[c] >= 0) msk |= 1 << bit[c];
+        msk = __reduce_or_sync(FULL, msk);
+        if (lane == 0 && msk) atomicOr(&sm.bits, msk);
         // Level shift D_s = max(0, a_s span): ln phi <= 0 inside a tile (the
         // baselines are the per-tile maxima) and 0 <= p <= span, so every
         // injection factor exp(ln phi + a_s p - D_s) is at most 1.
         (void)dl;
-        (void)lane;
         (void)w;
         if (tid < NB) sm.D[tid] = Engine::dshift(tid + 1, span);
 #pragma unroll
@@ -407,8 +416,12 @@ struct Engine {
         }
 #pragma unroll(UNR)
         for (int S = 0; S < NS; ++S) carry[S] = V(0);
+        rrp = &sm.rr[0][0];
     }
 
+    // F_T += phi * F_{T\k} at a point of bit k, in the f-representation of
+    // each state: the factor is the point's level factor times the tile's
+    // ratio of the two states' scales
     template <int SMAX, int KB>
     __device__ __forceinline__ void inject(int c)
     {
@@ -417,7 +430,7 @@ struct Engine {
             if (((T >> KB) & 1) && popc_c(T) <= SMAX) {
                 const int U = T ^ (1 << KB);
                 const V fu = (U == 0) ? V(1) : (carry[U] + run[U]);
-                run[T] = fma(fac[c][popc_c(T) - 1], fu, run[T]);
+                run[T] = fma(fac[c][popc_c(T) - 1] * rrp[T * NB + KB], fu, run[T]);
             }
         }
     }
@@ -539,7 +552,7 @@ struct Engine {
             own[q] = sf_zero<V>();
             acc[q] = sf_zero<V>();
             if (S < NS && popc_c(S) == s) {
-                own[q] = sf_scale_exp(sf_make<V>(sm.tot[S]), sum_beta(sm, S) + sm.gam[s]);
+                own[q] = sf_scale_exp(sf_mul(sf_make<V>(sm.tot[S]), sm.Gs[S]), sum_beta(sm, S));
                 sfp<V>(a.agg)[(size_t)v * NS + S] = sf_store(own[q]);
             }
         }
@@ -630,45 +643,69 @@ struct Engine {
         }
     }
 
-    // Choose the final scale of level s from the tile-end values and turn the
-    // tile carry into f-representation (warp 0).  Relative to exp(sum beta_S)
-    // the tile-end value is R_S = Eh_S + A_S exp(gamma_s); the new scale is
-    // 2^kmax with kmax the largest binary exponent of the R_S, so every
-    // level-s value becomes at most 1.  FP32 (or FP64) and integer work only.
+    // Provisional scales of the states of level s (warp 0): the largest scale
+    // of the states it is injected from, times exp(D_s), so every injection
+    // ratio rr[T][k] = scale(T\k) exp(D_s) / scale(T) is at most 1.
+    template <int s>
+    __device__ void prepare(Sm &sm)
+    {
+        const int lane = threadIdx.x & 31;
+        const Sf<V> eD = sf_make<V>(vexp<V>(sm.D[s - 1]));
+        for (int T = lane; T < NS; T += 32) {
+            if (popc_c(T) != s) continue;
+            // only sources that inject in this tile (a point of bit k present)
+            // choose the scale: the others would only push the real
+            // contributions out of range
+            Sf<V> mx = sf_zero<V>();
+            for (int k = 0; k < NB; ++k) {
+                if (!((T >> k) & 1) || !((sm.bits >> k) & 1)) continue;
+                const Sf<V> u = sm.Gs[T ^ (1 << k)];
+                if (mx.m == V(0) || u.k > mx.k || (u.k == mx.k && u.m > mx.m)) mx = u;
+            }
+            if (mx.m == V(0)) mx = Sf<V>{V(0.5), 1};   // no in-tile injection into T
+            const Sf<V> GP = sf_mul(mx, eD);
+            sm.Gs[T] = GP;
+            for (int k = 0; k < NB; ++k) {
+                V r = V(0);
+                if (((T >> k) & 1) && ((sm.bits >> k) & 1)) {
+                    const Sf<V> a = sf_mul(sm.Gs[T ^ (1 << k)], eD);
+                    r = (a.m / GP.m) * pow2neg<V>(a.k - GP.k);
+                }
+                sm.rr[T][k] = r;
+            }
+        }
+    }
+
+    // Final scale of each state of level s (warp 0): the tile-end value
+    // relative to exp(sum_{m in S} beta_m) is R_S = Eh_S + A_S scale_S, and the
+    // new scale is 2^k with k its binary exponent, so every value of the state
+    // becomes at most 1.  The carry turns into f-representation and the
+    // injection ratios into the state follow the rescale.  Each state has its
+    // own scale: states of one level may differ by far more than the FP32
+    // range (sparse supports at small eps).
     template <int s>
     __device__ void normalise(Sm &sm)
     {
         const int lane = threadIdx.x & 31;
-        constexpr int NQ = (NS + 31) / 32;
-        const Sf<V> G = sm.Gs[s];
-        int kmax = INT_MIN;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int S = lane + 32 * q;
-            if (S < NS && popc_c(S) == s) {
-                const Sf<V> R = sf_add(sm.Eh[S], sf_mul(sf_make<V>(sm.tot[S]), G));
-                if (R.m != V(0)) kmax = max(kmax, R.k);
+        for (int S = lane; S < NS; S += 32) {
+            if (popc_c(S) != s) continue;
+            const Sf<V> G = sm.Gs[S];
+            const Sf<V> A = sf_make<V>(sm.tot[S]);
+            const Sf<V> R = sf_add(sm.Eh[S], sf_mul(A, G));
+            V tc = V(0), rho = V(0);
+            if (R.m != V(0)) {
+                tc = sf_value(sm.Eh[S], R.k);
+                rho = (A.m == V(0)) ? V(0) : sf_value(G, R.k);
+                if (!(rho <= std::numeric_limits<V>::max())) rho = V(0);
+                sm.Gs[S] = Sf<V>{V(0.5), R.k + 1};
             }
+            sm.tc[S] = tc;
+            sm.rhoS[S] = rho;
+            for (int k = 0; k < NB; ++k) sm.rr[S][k] *= rho;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
-        const bool none = (kmax == INT_MIN);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int S = lane + 32 * q;
-            if (S < NS && popc_c(S) == s) sm.tc[S] = none ? V(0) : sf_value(sm.Eh[S], kmax);
-        }
-        if (lane == 0) {
-            sm.rho = none ? V(1) : sf_value(G, kmax);
-            const double gnew = none ? sm.gam[s] : (double)kmax * kLn2;
-            const Sf<V> Gn = none ? G : Sf<V>{V(0.5), kmax + 1};
-            sm.gam[s] = gnew;
-            sm.Gs[s] = Gn;
-            if (s < NB) {
-                const V Dn = sm.D[s];
-                sm.gam[s + 1] = gnew + (double)Dn;
-                sm.Gs[s + 1] = sf_mul(Gn, sf_make<V>(vexp<V>(Dn)));
-            }
+        if constexpr (s < NB) {
+            __syncwarp();
+            prepare<s + 1>(sm);
         }
     }
 
@@ -686,13 +723,9 @@ struct Engine {
             normalise<s>(sm);
         }
         __syncthreads();
-        const V rho = sm.rho;
 #pragma unroll
         for (int S = 0; S < NS; ++S)
-            if (popc_c(S) == s) carry[S] = sm.tc[S] + rho * excl[S];
-#pragma unroll
-        for (int c = 0; c < C; ++c) fac[c][s - 1] *= rho;
-        __syncthreads();
+            if (popc_c(S) == s) carry[S] = sm.tc[S] + sm.rhoS[S] * excl[S];
     }
 
     // ---- carry-free transfer operator of the chunk ------------------------
@@ -769,11 +802,11 @@ struct Engine {
     template <bool MAIN>
     __device__ void all_levels(Sm &sm, const SweepArgs &a, int v, int b, bool fwd)
     {
-        if (threadIdx.x == 0) {
-            sm.gam[0] = 0.0;
-            sm.Gs[0] = Sf<V>{V(0.5), 1};
-            sm.gam[1] = (double)sm.D[0];
-            sm.Gs[1] = sf_make<V>(vexp<V>(sm.D[0]));
+        __syncthreads();   // sm.bits complete (Engine::setup)
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) sm.Gs[0] = Sf<V>{V(0.5), 1};
+            __syncwarp();
+            prepare<1>(sm);
         }
         __syncthreads();
         static_for<1, NB + 1>([&](auto sc) {
@@ -807,6 +840,7 @@ __device__ void load_tile(SweepSmem<NB, V, NT, C, JCAP, WITH_G> &sm, const Sweep
         sm.mid[i] = __ldg(a.mid + t0 + i);
     }
     load_betas(sm, a, b, j);
+    if (threadIdx.x == 0) sm.bits = 0;
     __syncthreads();
 }
 
@@ -926,7 +960,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
             for (int U = 0; U < NS; ++U) sm.G[U * JCAP + sl] = (U == 0) ? V(1) : (e.carry[U] + e.run[U]);
         }
     });
-    if (tid <= NB) sm.gamG[tid] = sm.gam[tid];
+    for (int S = tid; S < NS; S += NT) sm.GsG[S] = sm.Gs[S];
     __syncthreads();
 
     // ---- forward states (look-back or stored carry), then combine ----------
@@ -942,53 +976,57 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
         e.template all_levels<false>(sm, a, v, b, true);
     }
 
-    // per-tile constants of the combine
+    // per-tile constants of the combine: binary exponent of the product of the
+    // two states' scales, and the FP64 base
     __shared__ double s_base;
-    __shared__ V s_dG[NB + 1];
+    for (int S = tid; S < NS; S += NT) sm.eS[S] = (sm.Gs[S].k - 1) + (sm.GsG[FULLS ^ S].k - 1);
     if (tid == 0) {
-        double gmx = -INFINITY;
-        for (int s = 0; s <= NB; ++s) gmx = fmax(gmx, sm.gam[s] + sm.gamG[NB - s]);
-        if (gmx == -INFINITY) gmx = 0.0;
         double sb = 0.0;
         for (int k = 0; k < NB; ++k) sb += sm.beta[k];
-        s_base = sb + gmx;
-        for (int s = 0; s <= NB; ++s) {
-            const double d = sm.gam[s] + sm.gamG[NB - s] - gmx;
-            s_dG[s] = (d < -1e30) ? V(-1e30) : (V)d;
-        }
+        s_base = sb;
     }
     __syncthreads();
-    // ln M = base + xM with the per-tile FP64 base and a small in-tile part
+    // ln M = base + xE ln 2 + xM: per-tile FP64 base, the binary exponent of
+    // the largest term and a small in-tile part.  Every term F_S G_{R\S} is
+    // formed as mantissa x 2^exponent, so terms whose states carry very
+    // different scales neither overflow nor underflow.
     V xM[C];
+    int xE[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) xM[c] = V(0);
+    for (int c = 0; c < C; ++c) {
+        xM[c] = V(0);
+        xE[c] = 0;
+    }
     const double base = s_base;
     e.template walk<NB>([&](int c) {
         const int sl = sm.slot[e.idx[c]];
-        V X[NB + 1];
-#pragma unroll
-        for (int s = 0; s <= NB; ++s) X[s] = V(0);
-        if (sl < JCAP) {
-#pragma unroll
-            for (int S = 0; S < NS; ++S) {
-                const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
-                X[popc_c(S)] += fS * sm.G[(FULLS ^ S) * JCAP + sl];
-            }
-        }
         const V pF = e.pp[c];
         const V pG = span - pF;
-        V ev[NB + 1];
-        V emax = V(-INFINITY);
+        V q[NB + 1];
 #pragma unroll
-        for (int s = 0; s <= NB; ++s) {
-            ev[s] = s_dG[s] - En::rate(s) * pF - En::rate(NB - s) * pG;
-            if (X[s] > V(0)) emax = (ev[s] > emax) ? ev[s] : emax;
-        }
+        for (int s = 0; s <= NB; ++s) q[s] = vexp<V>(-(En::rate(s) * pF + En::rate(NB - s) * pG));
+        int Emax = INT_MIN / 2;
         V sum = V(0);
-#pragma unroll
-        for (int s = 0; s <= NB; ++s)
-            if (X[s] > V(0)) sum += vexp<V>(ev[s] - emax) * X[s];
-        xM[c] = (sum > V(0)) ? emax + vlog<V>(sum) : V(-INFINITY);
+        if (sl < JCAP) {
+#pragma unroll(En::UNR)
+            for (int S = 0; S < NS; ++S) {
+                const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
+                const Sf<V> fm = sf_make<V>(fS);
+                const Sf<V> gm = sf_make<V>(sm.G[(FULLS ^ S) * JCAP + sl]);
+                if (fm.m != V(0) && gm.m != V(0)) {
+                    const V z = fm.m * gm.m * q[popc_c(S)];
+                    const int E = fm.k + gm.k + sm.eS[S];
+                    if (E > Emax) {
+                        sum = fma(sum, pow2neg<V>(Emax - E), z);
+                        Emax = E;
+                    } else {
+                        sum = fma(z, pow2neg<V>(E - Emax), sum);
+                    }
+                }
+            }
+        }
+        xM[c] = (sum > V(0)) ? vlog<V>(sum) : V(-INFINITY);
+        xE[c] = (sum > V(0)) ? Emax : 0;
     });
 
     // ---- FP64 epilogue ------------------------------------------------------
@@ -1006,7 +1044,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
             if (e.bit[c] == -1) {
                 const double lm = sm.lmu[sm.slot[e.idx[c]]];
                 if (lm > -INFINITY) {
-                    gq[c] = (lm - base) - (double)xM[c];
+                    gq[c] = (lm - base - (double)xE[c] * kLn2) - (double)xM[c];
                     if (!isfinite(gq[c])) bad = true;
                     qmax = fmax(qmax, (V)gq[c]);
                 }
@@ -1044,7 +1082,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
                 const int i = off + sm.slot[e.idx[c]];
                 const double gg = a.gj[i];
                 const double marg = (gg == -INFINITY || xM[c] == V(-INFINITY))
-                                        ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)xM[c]));
+                                        ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)xE[c] * kLn2 + (double)xM[c]));
                 acc += fabs(marg - a.muj[i]);
             }
         }
@@ -1062,7 +1100,7 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
         for (int c = 0; c < C; ++c) {
             if (e.bit[c] == -1) {
                 const int i = off + sm.slot[e.idx[c]];
-                const double lnMc = (xM[c] == V(-INFINITY)) ? -INFINITY : base + (double)xM[c];
+                const double lnMc = (xM[c] == V(-INFINITY)) ? -INFINITY : base + (double)xE[c] * kLn2 + (double)xM[c];
                 double r;
                 if (a.mode == MODE_OUT_M)
                     r = exp_acc<V>(lnMc);

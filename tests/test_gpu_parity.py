@@ -72,6 +72,54 @@ def test_marginal_product_parity(Plan, prec, l, N, eps, ties, zeros):
     plan.close()
 
 
+# sparse supports at small eps: neighbouring points lie tens of eps apart, so
+# states of one subset level differ by far more than the FP32 range
+SPARSE = [(4, 69, 1.2e-3, 176), (5, 160, 1.33e-3, 107), (6, 154, 1.27e-3, 255),
+          (7, 78, 1.46e-3, 49), (8, 82, 2.8e-3, 119), (3, 64, 1e-3, 7)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("l,N,eps,inst", SPARSE)
+def test_sparse_supports_small_eps(Plan, prec, l, N, eps, inst):
+    xs, mus = wl.batched_instance(inst, l, N)
+    gs = _init_g(xs, eps)
+    plan = Plan(xs, mus, eps, precision=prec)
+    for it in range(3):
+        for j in range(l):
+            ref = oracle.marginal_subset(xs, gs, eps, j)
+            got = plan.marginal(j, "lnM")
+            # a log value of magnitude L carries a rounding error of order u L
+            tol = TOL[prec] * max(1.0, 1e-2 * float(np.max(np.abs(ref))))
+            assert _lnM_err(got, ref) <= tol, (it, j, _lnM_err(got, ref))
+            gs[j] = oracle.potential_update(mus[j], ref, eps)
+            plan.set_potentials(j, gs[j])
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tiny_sparse_random(Plan, prec):
+    """Many tiny instances whose points lie tens to hundreds of eps apart:
+    every carry crosses a wide gap and each tile holds one to three points."""
+    rng = np.random.default_rng(2024)
+    worst = 0.0
+    for trial in range(150):
+        l = int(rng.integers(2, 7))
+        N = int(rng.integers(2, 9))
+        eps = float(10 ** rng.uniform(-3, -1.5))
+        xs = [np.sort(rng.random(N)) for _ in range(l)]
+        mus = [np.full(N, 1.0 / N) for _ in range(l)]
+        gs = _rand_g(xs, eps, seed=trial, scale=2 * eps)
+        plan = Plan(xs, mus, eps, precision=prec)
+        for k in range(l):
+            plan.set_potentials(k, gs[k])
+        for j in range(l):
+            ref = oracle.marginal_subset(xs, gs, eps, j)
+            err = _lnM_err(plan.marginal(j, "lnM"), ref)
+            worst = max(worst, err)
+            assert err <= TOL[prec] * max(1.0, 1e-2 * float(np.max(np.abs(ref)))), (trial, l, N, eps, j, err)
+        plan.close()
+
+
 OBJ_TOL = {"fp32": 2e-5, "fp64": 1e-11}
 
 
