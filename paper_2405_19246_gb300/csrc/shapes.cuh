@@ -4,8 +4,9 @@
 // The backward states of a tile are kept at its target points in shared memory
 // (NS x JCAP values), so K shrinks as the state count NS = 2^NB grows.
 // span_limit bounds max_s w_s * (x_last - x_first)/eps inside a tile, which
-// keeps every in-tile exponent small enough for the precision (FP32: the
-// exponent error is about 6e-8 * span_limit).
+// keeps every in-tile exponent small enough for the precision: the rounding
+// of a position enters an exponent as about u * span_limit (FP32: 6e-8 * 24;
+// FP64: 1.1e-16 * 50, so ln M keeps its 1e-12 bound).
 #pragma once
 #include "mmot_internal.cuh"
 
@@ -42,6 +43,6 @@ MMOT_SHAPE(7, double, 64, 1)
 #undef MMOT_SHAPE
 
 constexpr double kSpanLimitF32 = 24.0;
-constexpr double kSpanLimitF64 = 200.0;
+constexpr double kSpanLimitF64 = 50.0;
 
 }  // namespace mmot

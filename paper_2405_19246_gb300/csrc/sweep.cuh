@@ -360,6 +360,29 @@ struct Engine {
     V carry[NS];    // thread carries (f-representation), final levels only
     V run[NS];      // running local sums of the current walk
     const V *rrp;   // the tile's injection ratios (shared memory, [NS][NB])
+    // for few states the ratios of a walk are held in registers
+    static constexpr bool RREG = (NB <= 3);
+    V rrr[RREG ? NS : 1][RREG ? NB : 1];
+
+    __device__ __forceinline__ void load_ratios()
+    {
+        if constexpr (RREG) {
+#pragma unroll
+            for (int T = 0; T < NS; ++T)
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if ((T >> k) & 1) rrr[T][k] = rrp[T * NB + k];
+        }
+    }
+
+    template <int T, int KB>
+    __device__ __forceinline__ V ratio() const
+    {
+        if constexpr (RREG)
+            return rrr[T][KB];
+        else
+            return rrp[T * NB + KB];
+    }
 
     // rate w_s = s(l - s) with l = NB + 1
     __device__ static constexpr V rate(int s) { return (V)(s * (L - s)); }
@@ -425,12 +448,23 @@ struct Engine {
     template <int SMAX, int KB>
     __device__ __forceinline__ void inject(int c)
     {
+        if constexpr (RREG) {
+            static_for<0, NS>([&](auto tc) {
+                constexpr int T = decltype(tc)::value;
+                if constexpr (((T >> KB) & 1) && popc_c(T) <= SMAX) {
+                    constexpr int U = T ^ (1 << KB);
+                    const V fu = (U == 0) ? V(1) : (carry[U] + run[U]);
+                    run[T] = fma(fac[c][popc_c(T) - 1] * ratio<T, KB>(), fu, run[T]);
+                }
+            });
+        } else {
 #pragma unroll(UNR)
-        for (int T = 0; T < NS; ++T) {
-            if (((T >> KB) & 1) && popc_c(T) <= SMAX) {
-                const int U = T ^ (1 << KB);
-                const V fu = (U == 0) ? V(1) : (carry[U] + run[U]);
-                run[T] = fma(fac[c][popc_c(T) - 1] * rrp[T * NB + KB], fu, run[T]);
+            for (int T = 0; T < NS; ++T) {
+                if (((T >> KB) & 1) && popc_c(T) <= SMAX) {
+                    const int U = T ^ (1 << KB);
+                    const V fu = (U == 0) ? V(1) : (carry[U] + run[U]);
+                    run[T] = fma(fac[c][popc_c(T) - 1] * rrp[T * NB + KB], fu, run[T]);
+                }
             }
         }
     }
@@ -451,6 +485,7 @@ struct Engine {
     template <int SMAX, typename OnT>
     __device__ __forceinline__ void walk(OnT &&on_target)
     {
+        load_ratios();
 #pragma unroll(UNR)
         for (int S = 0; S < NS; ++S) run[S] = V(0);
 #pragma unroll
@@ -468,6 +503,7 @@ struct Engine {
     template <bool PRE, typename OnP>
     __device__ __forceinline__ void walk_each(OnP &&on_point)
     {
+        load_ratios();
 #pragma unroll(UNR)
         for (int S = 0; S < NS; ++S) run[S] = V(0);
 #pragma unroll
