@@ -138,8 +138,10 @@ mmot_status mmot_set_option(mmot_plan p, int option, int64_t value);
 /* Per-kernel launch statistics collected while MMOT_OPT_PROFILE is on.
  *   kernel 0: backward look-back scan (k_bwd), 1: forward look-back scan +
  *   combine (k_fwd), 2: tile transfer operators (k_tileop), 3: carry scan over
- *   tiles (k_carry), 4: tile products with known carries + combine (k_prod).
- *   Plans with l <= 5 use kernels 2-4, larger l kernels 0-1.
+ *   tiles (k_carry), 4: tile products with known carries + combine (k_prod),
+ *   5: per-level tile contributions (k_lagg), 6: per-level carry scan
+ *   (k_lscan).  Marginal products use kernels 2-4 for l <= 5 and 4-6 for
+ *   l >= 6; kernels 0-1 serve the objective sweeps of l >= 5.
  * Returns the number of launches and their summed device time in ms (CUDA
  * events on the plan's stream); synchronises the stream.  reset != 0 clears
  * the statistics after reading. */
@@ -196,7 +198,8 @@ void mmot_destroy(mmot_plan p);
  * after another in one merged order whose tiles never straddle two instances
  * and across whose boundaries no state is carried, so every kernel launch of
  * a Sinkhorn iteration serves all instances of that l at once; each l forms a
- * group with its own launch sequence, all on the batch's stream.  Each
+ * group with its own launch sequence (split into consecutive parts above
+ * 65536 tiles for l <= 5), all on the batch's stream.  Each
  * instance stops on its own: after every check its residual (marginals
  * 1..l-1, as in mmot_sinkhorn_step) is compared with tol and a converged
  * instance is frozen (no further updates; its potentials stay as they were
@@ -243,7 +246,8 @@ mmot_status mmot_batch_get_potentials(mmot_batch b, int i, int k, double *g_out)
 
 typedef struct {
     int instances;
-    int groups;                /* distinct l                                    */
+    int groups;                /* launch groups: one per l, split into parts when
+                                  one carry scan cannot take all its tiles     */
     int64_t total_points;
     int64_t tiles;
     int64_t kernel_launches;   /* library kernels launched on this batch so far */

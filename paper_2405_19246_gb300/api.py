@@ -141,12 +141,13 @@ class Plan:
     def profile_stats(self, reset=True):
         """{kernel name: (launches, total ms)} from the CUDA-event profile."""
         out = {}
-        names = ((0, "k_bwd"), (1, "k_fwd"), (2, "k_tileop"), (3, "k_carry"), (4, "k_prod"))
+        names = ((0, "k_bwd"), (1, "k_fwd"), (2, "k_tileop"), (3, "k_carry"), (4, "k_prod"),
+                 (5, "k_lagg"), (6, "k_lscan"))
         for k, name in names:
             n = ctypes.c_int64()
             ms = ctypes.c_double()
             nat.check(nat.lib().mmot_get_profile(self._h, k, ctypes.byref(n), ctypes.byref(ms),
-                                                 1 if (reset and k == 4) else 0))
+                                                 1 if (reset and k == 6) else 0))
             out[name] = (n.value, ms.value)
         return out
 

@@ -170,7 +170,8 @@ struct mmot_plan_s {
     unsigned char *agg = nullptr, *inc = nullptr, *bcarry = nullptr;
     unsigned char *fcarry = nullptr, *opF = nullptr, *opB = nullptr;
     unsigned char *pdecF = nullptr, *pdecB = nullptr;
-    int *cflags = nullptr;          // carry-scan chunk flags [2][32][NB+1]
+    int *cflags = nullptr;          // carry-scan chunk flags
+    size_t cflags_n = 0;
     unsigned char *cagg = nullptr;  // carry-scan chunk contributions [2][32][NS]
     size_t sfsz = 8;
     bool three_phase = false;  // tile operators + carry scan (l <= 5)
@@ -196,9 +197,9 @@ struct mmot_plan_s {
     int profile = 0;
     struct Rec { int kernel; cudaEvent_t a, b; };
     std::vector<Rec> recs;
-    int64_t prof_count[5] = {0, 0, 0, 0, 0};
+    int64_t prof_count[7] = {0, 0, 0, 0, 0, 0, 0};
     int64_t launches = 0;   // kernels launched so far (graph replays included)
-    double prof_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double prof_ms[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 
     ~mmot_plan_s()
     {
@@ -225,27 +226,6 @@ struct mmot_plan_s {
 };
 
 namespace {
-
-template <int NB>
-cudaError_t launch_pair_nb(const SweepArgs &a, bool fp64, cudaStream_t st, bool fwd)
-{
-    if (fp64) return fwd ? launch_fwd<NB, double>(a, st) : launch_bwd<NB, double>(a, st);
-    return fwd ? launch_fwd<NB, float>(a, st) : launch_bwd<NB, float>(a, st);
-}
-
-cudaError_t launch_sweep(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, bool fwd)
-{
-    switch (NB) {
-    case 1: return launch_pair_nb<1>(a, fp64, st, fwd);
-    case 2: return launch_pair_nb<2>(a, fp64, st, fwd);
-    case 3: return launch_pair_nb<3>(a, fp64, st, fwd);
-    case 4: return launch_pair_nb<4>(a, fp64, st, fwd);
-    case 5: return launch_pair_nb<5>(a, fp64, st, fwd);
-    case 6: return launch_pair_nb<6>(a, fp64, st, fwd);
-    case 7: return launch_pair_nb<7>(a, fp64, st, fwd);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 // kind: 2 tile operators, 3 carry scan, 4 product
 template <int NB>
@@ -280,9 +260,41 @@ cudaError_t mmot::launch_three_phase(int NB, const SweepArgs &a, bool fp64, cuda
 
 namespace {
 
+// kind 4: tile products (all NB); 5: level contributions, 6: level scan (NB >= 5)
+template <int NB>
+cudaError_t launch_lvl_nb(const SweepArgs &a, bool fp64, cudaStream_t st, int kind, int SL, int fwd)
+{
+    if constexpr (NB > kMaxOpBits) {
+        if (kind == 4) return fp64 ? launch_prod<NB, double>(a, st) : launch_prod<NB, float>(a, st);
+        if (kind == 5) return fp64 ? launch_lagg<NB, double>(a, st, SL, fwd) : launch_lagg<NB, float>(a, st, SL, fwd);
+        if (kind == 6) return fp64 ? launch_lscan<NB, double>(a, st, SL, fwd) : launch_lscan<NB, float>(a, st, SL, fwd);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_levels(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind, int SL, int fwd)
+{
+    switch (NB) {
+    case 5: return launch_lvl_nb<5>(a, fp64, st, kind, SL, fwd);
+    case 6: return launch_lvl_nb<6>(a, fp64, st, kind, SL, fwd);
+    case 7: return launch_lvl_nb<7>(a, fp64, st, kind, SL, fwd);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_ops(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
 {
     return mmot::launch_three_phase(NB, a, fp64, st, kind);
+}
+
+template <typename V>
+int wshape_k(int NB)
+{
+    switch (NB) {
+    case 5: return WShape<5, V>::K;
+    case 6: return WShape<6, V>::K;
+    default: return WShape<7, V>::K;
+    }
 }
 
 template <int NB>
@@ -359,13 +371,18 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     return a;
 }
 
-// kernel ids: 0 k_bwd, 1 k_fwd (look-back design); 2 k_tileop, 3 k_carry,
-// 4 k_prod (three-phase design)
-mmot_status timed_launch(mmot_plan p, int kernel, const SweepArgs &a, bool fp64)
+// kernels per marginal product in an iteration: carry scan + tile products
+// (three-phase, l <= 5), or 2 (NB levels x contribution + scan) + products
+int launches_per_product(mmot_plan p) { return p->three_phase ? 2 : 4 * p->NB + 1; }
+
+// kernel ids: 2 k_tileop, 3 k_carry, 4 k_prod (three-phase design, l <= 5);
+// 5 k_wpass, 6 k_lscan, 4 k_wprod (level passes and warp tiles, l >= 6);
+// 0, 1 are not used by marginal products (objective sweeps only)
+mmot_status timed_launch(mmot_plan p, int kernel, const SweepArgs &a, bool fp64, int SL = 0, int fwd = 0)
 {
     p->launches += 1;
     auto go = [&]() -> cudaError_t {
-        if (kernel <= 1) return launch_sweep(p->NB, a, fp64, p->st, kernel == 1);
+        if (p->NB > kMaxOpBits) return launch_levels(p->NB, a, fp64, p->st, kernel, SL, fwd);
         return launch_ops(p->NB, a, fp64, p->st, kernel);
     };
     if (!p->profile) {
@@ -402,7 +419,7 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
             if (s != MMOT_OK) return s;
             p->ops_target = j;
         }
-        CUDA_TRY(cudaMemsetAsync(p->cflags, 0, sizeof(int) * 2 * 32 * (p->NB + 1), p->st));
+        CUDA_TRY(cudaMemsetAsync(p->cflags, 0, sizeof(int) * p->cflags_n, p->st));
         s = timed_launch(p, 3, a, fp64);
         if (s != MMOT_OK) return s;
         a.jnext = (mode == MODE_UPDATE) ? jnext : -1;
@@ -411,11 +428,18 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
         if (a.jnext >= 0) p->ops_target = a.jnext;
         return MMOT_OK;
     }
-    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
-    mmot_status s = timed_launch(p, 0, a, fp64);
-    if (s != MMOT_OK) return s;
-    CUDA_TRY(cudaMemsetAsync(p->flags, 0, p->flags_bytes, p->st));
-    return timed_launch(p, 1, a, fp64);
+    // level passes: backward and forward carries level by level, then the
+    // tile products with both carries known
+    CUDA_TRY(cudaMemsetAsync(p->cflags, 0, sizeof(int) * p->cflags_n, p->st));
+    for (int fwd = 0; fwd < 2; ++fwd) {
+        for (int lv = 1; lv <= p->NB; ++lv) {
+            mmot_status s = timed_launch(p, 5, a, fp64, lv, fwd);
+            if (s != MMOT_OK) return s;
+            s = timed_launch(p, 6, a, fp64, lv, fwd);
+            if (s != MMOT_OK) return s;
+        }
+    }
+    return timed_launch(p, 4, a, fp64);
 }
 
 template <int Lm>
@@ -633,6 +657,9 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
 
 // Plan of one instance, or of a batch of independent instances with the same
 // l laid out one after the other (tiles never straddle two instances).
+// tiles one carry scan handles (k_carry: 32 chunks x 256 threads x 8 tiles)
+constexpr int kMaxCarryTiles = 32 * 256 * 8;
+
 mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision prec, int inputs_on_device,
                        void *cuda_stream, mmot_plan *out, int tile_points = 0, bool batch = false)
 {
@@ -661,6 +688,11 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     const bool fp64 = (prec == MMOT_FP64);
     int K = 0, NT = 0, jcap = 0;
     shape_of(l - 1, fp64, &K, &NT, &jcap);
+    if (l - 1 > kMaxOpBits) {
+        // warp-tile products (warp.cuh)
+        K = fp64 ? wshape_k<double>(l - 1) : wshape_k<float>(l - 1);
+        jcap = K / 2;
+    }
     if (tile_points > 0) K = std::max(32, std::min(K, tile_points));
     const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
     HostLayout L;
@@ -709,6 +741,8 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         seg_tile0.push_back(L.nt);
     }
 
+    if (l - 1 <= kMaxOpBits && L.nt > kMaxCarryTiles)
+        return fail(MMOT_ERR_RANGE, "%d tiles exceed the carry scan's %d", L.nt, kMaxCarryTiles);
     mmot_plan p = new (std::nothrow) mmot_plan_s();
     if (!p) return fail(MMOT_ERR_OOM, "host allocation failed");
     p->l = l;
@@ -794,14 +828,17 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     PA(p->inc, (size_t)nt * p->NS * p->sfsz);
     PA(p->bcarry, (size_t)nt * p->NS * p->sfsz);
     p->three_phase = (p->NB <= kMaxOpBits);
+    PA(p->fcarry, (size_t)nt * p->NS * p->sfsz);
+    PA(p->pdecF, (size_t)nt * (p->NB + 1) * p->sfsz);
+    PA(p->pdecB, (size_t)nt * (p->NB + 1) * p->sfsz);
+    // chunk flags / contributions: [2][32][NB+1] (three-phase scan) or
+    // [2][NS][32] (one scalar scan per state, level passes)
+    p->cflags_n = p->three_phase ? (size_t)2 * 32 * (p->NB + 1) : (size_t)2 * p->NS * 32;
+    PA(p->cflags, p->cflags_n);
+    PA(p->cagg, (size_t)2 * 32 * p->NS * p->sfsz);
     if (p->three_phase) {
-        PA(p->fcarry, (size_t)nt * p->NS * p->sfsz);
         PA(p->opF, (size_t)nt * p->NB * p->NS * p->sfsz);
         PA(p->opB, (size_t)nt * p->NB * p->NS * p->sfsz);
-        PA(p->pdecF, (size_t)nt * (p->NB + 1) * p->sfsz);
-        PA(p->pdecB, (size_t)nt * (p->NB + 1) * p->sfsz);
-        PA(p->cflags, (size_t)2 * 32 * (p->NB + 1));
-        PA(p->cagg, (size_t)2 * 32 * p->NS * p->sfsz);
     }
     PA(p->partial, nt);
     p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);
@@ -842,11 +879,9 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     std::vector<unsigned char> hdecF, hdecB;
     const std::vector<int32_t> segv = batch ? hseg : std::vector<int32_t>();
     if (l <= kMaxOpBits) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB, segv);
-    if (p->three_phase) {
-        decay_tables(L, p->NB, fp64, hdecF, hdecB, segv);
-        ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
-        ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());
-    }
+    decay_tables(L, p->NB, fp64, hdecF, hdecB, segv);
+    ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
+    ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());
     ce = ce ? ce : up(p->span, hspan.data(), sizeof(double) * nt);
     ce = ce ? ce : up(p->cnt, hcnt.data(), sizeof(int32_t) * nt * l);
     ce = ce ? ce : up(p->reftile, href.data(), sizeof(int32_t) * nt * l);
@@ -875,6 +910,9 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         ce = ce ? ce : up(p->d_g0, g0.data(), sizeof(double) * g0.size());
         ce = ce ? ce : cudaMemsetAsync(p->d_frozen, 0, sizeof(int32_t) * nin, p->st);
     }
+    // carries of the empty state are never written by the level scans
+    ce = ce ? ce : cudaMemsetAsync(p->fcarry, 0, (size_t)nt * p->NS * p->sfsz, p->st);
+    ce = ce ? ce : cudaMemsetAsync(p->bcarry, 0, (size_t)nt * p->NS * p->sfsz, p->st);
     ce = ce ? ce : cudaMemsetAsync(p->err, 0, sizeof(int), p->st);
     ce = ce ? ce : cudaStreamSynchronize(p->st);
     if (ce != cudaSuccess) {
@@ -1019,7 +1057,7 @@ mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out)
             }
             for (int it = 0; it < n_iters; ++it) {
                 CUDA_TRY(cudaGraphLaunch(p->graph, p->st));
-                p->launches += 2 * p->l;
+                p->launches += (int64_t)p->l * launches_per_product(p);
             }
         } else {
             for (int it = 0; it < n_iters; ++it) {
@@ -1150,7 +1188,7 @@ mmot_status mmot_reset_potentials(mmot_plan p)
 mmot_status mmot_get_profile(mmot_plan p, int kernel, int64_t *launches, double *total_ms, int reset)
 {
     if (!p || !launches || !total_ms) return fail(MMOT_ERR_INVALID_ARG, "NULL argument");
-    if (kernel < 0 || kernel > 4) return fail(MMOT_ERR_INVALID_ARG, "kernel must be in 0..4");
+    if (kernel < 0 || kernel > 6) return fail(MMOT_ERR_INVALID_ARG, "kernel must be in 0..6");
     CUDA_TRY(cudaStreamSynchronize(p->st));
     for (auto &r : p->recs) {
         float ms = 0.f;
@@ -1164,7 +1202,7 @@ mmot_status mmot_get_profile(mmot_plan p, int kernel, int64_t *launches, double 
     *launches = p->prof_count[kernel];
     *total_ms = p->prof_ms[kernel];
     if (reset) {
-        for (int q = 0; q < 5; ++q) {
+        for (int q = 0; q < 7; ++q) {
             p->prof_count[q] = 0;
             p->prof_ms[q] = 0.0;
         }
@@ -1179,7 +1217,7 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
     info->tiles = p->nt;
     info->tile_points = p->K;
     info->threads_per_block = p->NT;
-    info->launches_per_iteration = 2 * p->l;   // both designs: two kernels per product
+    info->launches_per_iteration = p->l * launches_per_product(p);
     info->precision = p->prec;
     info->kernel_launches = p->launches;
     return MMOT_OK;
@@ -1308,22 +1346,35 @@ mmot_status mmot_batch_create(int n, const int *l, const int64_t *N, const doubl
             idx.push_back(i);
         }
         if (ins.empty()) continue;
-        mmot_batch_s::Group G;
-        G.l = L;
-        mmot_status s = plan_build(L, ins, prec, 0, b->st, &G.p, tile_points, true);
-        if (s != MMOT_OK) {
-            // report the batch index of a failing instance
-            std::string m = g_last_error;
-            delete b;
-            return fail(s, "l = %d group: %s", L, m.c_str());
-        }
-        G.inst = idx;
-        for (size_t q = 0; q < idx.size(); ++q) b->where[idx[q]] = {(int)b->groups.size(), (int)q};
-        b->groups.push_back(G);
-        s = group_reset(b->groups.back());
-        if (s != MMOT_OK) {
-            delete b;
-            return s;
+        // one group per l; a group with more tiles than one carry scan takes
+        // is split into consecutive parts
+        std::vector<std::pair<size_t, size_t>> todo{{0, ins.size()}};
+        while (!todo.empty()) {
+            const auto r = todo.back();
+            todo.pop_back();
+            std::vector<InstanceIn> part(ins.begin() + r.first, ins.begin() + r.second);
+            mmot_batch_s::Group G;
+            G.l = L;
+            mmot_status s = plan_build(L, part, prec, 0, b->st, &G.p, tile_points, true);
+            if (s == MMOT_ERR_RANGE && r.second - r.first > 1) {
+                const size_t mid = (r.first + r.second) / 2;
+                todo.push_back({mid, r.second});
+                todo.push_back({r.first, mid});
+                continue;
+            }
+            if (s != MMOT_OK) {
+                std::string m = g_last_error;
+                delete b;
+                return fail(s, "l = %d group: %s", L, m.c_str());
+            }
+            G.inst.assign(idx.begin() + r.first, idx.begin() + r.second);
+            for (size_t q = 0; q < G.inst.size(); ++q) b->where[G.inst[q]] = {(int)b->groups.size(), (int)q};
+            b->groups.push_back(G);
+            s = group_reset(b->groups.back());
+            if (s != MMOT_OK) {
+                delete b;
+                return s;
+            }
         }
     }
     *out = b;

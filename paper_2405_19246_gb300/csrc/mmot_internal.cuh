@@ -98,11 +98,6 @@ struct SweepArgs {
 __host__ __device__ inline double tile_eps(const SweepArgs &a, int b) { return a.teps ? a.teps[b] : a.eps; }
 
 // Host-side launchers (one per bit count NB = l-1, instantiated per precision).
-// Look-back design (every l): k_bwd then k_fwd.
-template <int NB, typename V>
-cudaError_t launch_bwd(const SweepArgs &a, cudaStream_t s);
-template <int NB, typename V>
-cudaError_t launch_fwd(const SweepArgs &a, cudaStream_t s);
 // Three-phase design (l <= 5): tile operators, carry scan over tiles, tile
 // products with known carries (optionally followed by the operators of a.jnext).
 template <int NB, typename V>
@@ -111,6 +106,11 @@ template <int NB, typename V>
 cudaError_t launch_carry(const SweepArgs &a, cudaStream_t s);
 template <int NB, typename V>
 cudaError_t launch_prod(const SweepArgs &a, cudaStream_t s);
+// Level passes (l >= 6): tile contributions of one level, scalar carry scan.
+template <int NB, typename V>
+cudaError_t launch_lagg(const SweepArgs &a, cudaStream_t s, int level, int fwd);
+template <int NB, typename V>
+cudaError_t launch_lscan(const SweepArgs &a, cudaStream_t s, int level, int fwd);
 constexpr int kMaxOpBits = 4;
 // message for mmot_last_error (defined in mmot.cu)
 }  // namespace mmot

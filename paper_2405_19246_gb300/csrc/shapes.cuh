@@ -42,6 +42,14 @@ MMOT_SHAPE(6, double, 128, 1)
 MMOT_SHAPE(7, double, 64, 1)
 #undef MMOT_SHAPE
 
+// points per warp tile of the products with l >= 6 (warp.cuh; the plan's
+// tiling uses at most this many, half of them of one marginal)
+template <int NB, typename V>
+struct WShape {
+    static constexpr int K = (sizeof(V) == 4) ? (NB <= 5 ? 128 : 64) : (NB <= 5 ? 64 : 32);
+    static constexpr int JCAP = K / 2;
+};
+
 constexpr double kSpanLimitF32 = 24.0;
 constexpr double kSpanLimitF64 = 50.0;
 

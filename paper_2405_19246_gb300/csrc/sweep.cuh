@@ -1,6 +1,6 @@
 // Sweep kernels: the marginal product M_j of l-marginal Sinkhorn with L1 cost
-// (arXiv 2405.19246, Sec. 3 and Sec. 4.2) as a level-pipelined, decoupled
-// look-back scan over tiles of the merged support order.
+// (arXiv 2405.19246, Sec. 3 and Sec. 4.2) as scans over tiles of the merged
+// support order.
 //
 // What is computed.  For target j and every subset S of R = [l]\{j}:
 //   F_S(x) = sum over placements of one point of each marginal of S, all
@@ -11,29 +11,27 @@
 // only injects
 //     F~_T += phi_m exp((w_s - w_{s-1}) pos_t) F~_{T\m}   for every T containing m,
 // which is the paper's recurrences J = lambda^2 J + psi P (Algorithm 2) with the
-// multipliers moved into the frame.  Level s = |T| depends on level s-1 at the
-// same point, so the scan runs level by level: for s = 1..l-1 each tile
-//   1. walks its points (each thread a contiguous chunk) recomputing levels
-//      1..s from the final lower-level carries,
-//   2. block-scans the level-s chunk totals,
-//   3. publishes its level-s aggregate (FP64 log domain) and looks back over
-//      the preceding tiles for its exclusive carry (decoupled look-back over
-//      the associative pairs (decay, offset); the decay of level s over a
-//      distance d is exp(-w_s d/eps), the same for every state of the level),
-//   4. renormalises level s so that its largest tile-end value is 1.
-// Values inside a tile are FP32 (or FP64) "f-representations"
-//     f_S = F~_S exp(-sum_{m in S} beta_m - gamma_{|S|})
-// with per-tile FP64 baselines beta_m (from the potentials; the re-centring of
-// Algorithm 5) and per-level scales gamma_s.  Carries between tiles are FP64
-// logarithms.
+// multipliers moved into the frame.
 //
-// The backward states G are the mirror image.  k_bwd runs the backward scan
-// and stores each tile's backward carry; k_fwd recomputes the tile's backward
-// states from that carry (no look-back), keeps them at the target points in
-// shared memory, runs the forward scan with look-back and combines
+// Block engine (Engine, one tile per CTA, each thread a contiguous chunk of
+// points; l <= 5).  Level s = |T| depends on level s-1 at the same point, so a
+// tile runs level by level: walk the points recomputing levels 1..s from the
+// final lower-level values, block-scan the level-s chunk totals, take the
+// level's carries, then give every state of the level its own scale (the
+// largest tile-end value of the state becomes 1).  Values inside a tile are
+// FP32 (or FP64) "f-representations" F~_S exp(-sum_{m in S} beta_m) / scale_S
+// with per-tile FP64 baselines beta_m (the re-centring of Algorithm 5).
+// Carries between tiles are scaled floats (mantissa, binary exponent).
+//
+// Three-phase product (l <= 5): k_tileop computes every tile's carry-free
+// transfer operator, k_carry scans the operators over the tiles for the exact
+// carries, k_prod recomputes each tile from its forward and backward carries,
+// keeps the backward states at the target points in shared memory, combines
 //     M_j(i) = sum_S F_S(x_i^-) G_{R\S}(x_i^+)
-// at the target points, then applies the FP64 epilogue (potential update
-// g_j = eps (ln mu_j - ln M_j), or an output mode).
+// at the target points and applies the FP64 epilogue (potential update
+// g_j = eps (ln mu_j - ln M_j), residual, or an output mode).  Products with
+// l >= 6 use warp tiles and level passes (warp.cuh); the look-back scan of
+// the Engine (lookback, k_bwd) serves the objective sweeps (objective.cuh).
 #pragma once
 #include <limits>
 #include <climits>
@@ -598,12 +596,10 @@ struct Engine {
         if (lane == 0) st_release(myflag, 1);
         bool fail = false;
         const double ub = fwd ? a.ulb[b] : a.urb[b];
-        // every lane accumulates the terms of the predecessors it inspects;
-        // one warp reduction per state at the end
-        constexpr int NL = NS;   // per-state lane-local sums (only level s used)
-        Sf<V> part[NL];
-#pragma unroll
-        for (int S = 0; S < NL; ++S) part[S] = sf_zero<V>();
+        // lane i inspects predecessor base - i (flag and decay); the terms are
+        // then gathered state-parallel: for each predecessor in the window every
+        // lane adds the values of its own states (S = lane + 32q), so no
+        // reduction across lanes is needed
         const int myseg = a.seg ? a.seg[b] : 0;
         int base = v - 1;
         while (base >= 0) {
@@ -631,36 +627,41 @@ struct Engine {
                 fail = true;
                 break;
             }
-            if (lane <= first && p >= 0 && !other) {
+            // decay exp(-w_s d) of this lane's predecessor as (fraction, power of two)
+            V dm = V(0);
+            int dk = INT_MIN / 2;
+            if (p >= 0 && !other) {
                 const int bp = fwd ? p : a.nt - 1 - p;
                 const double d = fwd ? (ub - a.ulb[bp]) : (a.urb[bp] - ub);
-                // decay exp(-w_s d) as (fraction, integer) of a power of two
                 const double y = -ws * d * kLog2e;
-                const double n = floor(y);
-                const V dm = vexp2<V>((V)(y - n));
-                const int dk = (y < -1.0e9) ? INT_MIN / 2 : (int)n;
-                const SfT<V> *src = sfp<V>((f == 2) ? a.inc : a.agg);
+                if (y >= -1.0e9) {
+                    const double n = floor(y);
+                    dm = vexp2<V>((V)(y - n));
+                    dk = (int)n;
+                }
+            }
+            for (int i = 0; i <= first; ++i) {
+                const int pi = __shfl_sync(FULL, p, i);
+                const int fi = __shfl_sync(FULL, f, i);
+                const V dmi = __shfl_sync(FULL, dm, i);
+                const int dki = __shfl_sync(FULL, dk, i);
+                if (pi < 0 || dmi == V(0)) continue;   // none, another instance or no decay left
+                const SfT<V> *src = sfp<V>((fi == 2) ? a.inc : a.agg) + (size_t)pi * NS;
 #pragma unroll
-                for (int S = 0; S < NS; ++S) {
-                    if (popc_c(S) == s) {
-                        const Sf<V> raw = sf_load<V>(__ldcg(src + (size_t)p * NS + S));
-                        if (raw.m != V(0) && dk > INT_MIN / 2) {
-                            Sf<V> t = sf_make<V>(raw.m * dm);
-                            t.k += raw.k + dk;
-                            part[S] = sf_add(part[S], t);
+                for (int q = 0; q < NQ; ++q) {
+                    const int S = lane + 32 * q;
+                    if (S < NS && popc_c(S) == s) {
+                        const Sf<V> raw = sf_load<V>(__ldcg(src + S));
+                        if (raw.m != V(0)) {
+                            Sf<V> t = sf_make<V>(raw.m * dmi);
+                            t.k += raw.k + dki;
+                            acc[q] = sf_add(acc[q], t);
                         }
                     }
                 }
             }
             if (incl) break;
             base -= 32;
-        }
-#pragma unroll
-        for (int S = 0; S < NS; ++S) {
-            if (popc_c(S) == s) {
-                const Sf<V> t = sf_warp_sum(part[S]);
-                if (lane == (S & 31)) acc[S >> 5] = t;
-            }
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -1151,21 +1152,6 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
     __syncthreads();
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
-__global__ void __launch_bounds__(NT) k_fwd(SweepArgs a)
-{
-    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Sm &sm = *reinterpret_cast<Sm *>(smraw);
-    __shared__ int s_v;
-    if (threadIdx.x == 0) s_v = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int v = s_v;
-    if (v >= a.nt) return;
-    if (skip_tile(a, v)) return;
-    product_body<NB, V, NT, C, JCAP, true>(sm, a, v, v);
-}
-
 // Carry-free transfer operator of tile b for target j in one direction,
 // stored as scaled floats with the decay to the next tile base (processing
 // order) included:
@@ -1293,14 +1279,183 @@ __global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
     const int b = blockIdx.x;
     if (skip_tile(a, b)) return;
     product_body<NB, V, NT, C, JCAP, false>(sm, a, b, b);
-    if (a.jnext >= 0) {
-        // operators of the next target from the updated potentials of this tile
-        const uint32_t t0 = a.tstart[b];
-        const int n = (int)(a.tstart[b + 1] - t0);
-        load_betas(sm, a, b, a.jnext);
-        __syncthreads();
-        tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, true);
-        tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, false);
+    if constexpr (NB <= kMaxOpBits) {
+        if (a.jnext >= 0) {
+            // operators of the next target from the updated potentials of this tile
+            const uint32_t t0 = a.tstart[b];
+            const int n = (int)(a.tstart[b + 1] - t0);
+            load_betas(sm, a, b, a.jnext);
+            __syncthreads();
+            tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, true);
+            tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, false);
+        }
+    }
+}
+
+// ---- level passes (many state bits) -----------------------------------------
+// For l >= 6 the carries of level s are computed in one pass per level and
+// direction: every tile evaluates its own contribution to the states of level
+// s at its base, given the (already known) carries of the lower levels
+// (k_wpass, warp.cuh), and one scalar affine scan per state over the tiles
+// turns those contributions into every tile's carry (k_lscan):
+//   E_T(next base) = exp(-w_s d) (E_T + own_T).
+// No tile waits on another tile; the scans wait only on earlier chunks.
+// Scalar carry scan of one state of level SL over the tiles (processing
+// order): blockIdx.y picks the state, blockIdx.x the chunk of tiles.  Each
+// thread composes the maps x -> dec (x + own) of its tiles, the block scans
+// them, the chunk publishes its contribution at the next chunk's base and
+// adds those of the earlier chunks (same instance only; bounded waits).
+template <int NB, typename V>
+__global__ void __launch_bounds__(256) k_lscan(SweepArgs a, int SL, int fwd_i)
+{
+    constexpr int NS = 1 << NB;
+    constexpr int NTB = 256;
+    constexpr int NWB = NTB / 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    const bool fwd = (fwd_i != 0);
+    const int G = gridDim.x, c = blockIdx.x;
+    // the state of level SL this block scans
+    int T = 0;
+    for (int S = 1, q = 0; S < NS; ++S) {
+        if (popc_c(S) != SL) continue;
+        if (q == (int)blockIdx.y) {
+            T = S;
+            break;
+        }
+        ++q;
+    }
+    const SfT<V> *__restrict__ own = sfp<V>(a.agg);
+    const SfT<V> *__restrict__ pdec = sfp<V>(fwd ? a.pdecF : a.pdecB);
+    SfT<V> *E = sfp<V>(fwd ? a.fcarry : a.bcarry);
+    const int slot = ((fwd ? 0 : 1) * NS + T) * 32;
+    SfT<V> *cagg = sfp<V>(a.cagg) + slot;
+    int *cflag = a.cflags + slot;
+    const int nt = a.nt, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int Rc = (nt + G - 1) / G;
+    const int cv0 = min(nt, c * Rc), cv1 = min(nt, cv0 + Rc);
+    const int R = (cv1 - cv0 + NTB - 1) / NTB;
+    const int v0 = min(cv1, cv0 + tid * R), v1 = min(cv1, v0 + R);
+    auto tile_of = [&](int v) { return fwd ? v : nt - 1 - v; };
+    auto chunk_base = [&](int q) -> double {
+        const int v = min(nt - 1, q * Rc);
+        return fwd ? a.ulb[tile_of(v)] : a.urb[tile_of(v)];
+    };
+    __shared__ V s_am[NWB], s_bm[NWB];
+    __shared__ int s_ak[NWB], s_bk[NWB];
+    __shared__ V s_em;
+    __shared__ int s_ek;
+    // pass 1: this thread's map x -> am x + bb
+    Sf<V> am = Sf<V>{V(0.5), 1}, bb = sf_zero<V>();
+    for (int v = v0; v < v1; ++v) {
+        const int b = tile_of(v);
+        const Sf<V> dec = sf_load<V>(__ldg(pdec + (size_t)b * (NB + 1) + SL));
+        const Sf<V> o = sf_load<V>(__ldcg(own + (size_t)b * NS + T));
+        bb = sf_mul(sf_add(bb, o), dec);
+        am = sf_mul(am, dec);
+    }
+    // inclusive scan of the maps across the warp, then across warps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Sf<V> oa, ob;
+        oa.m = __shfl_up_sync(FULL, am.m, o);
+        oa.k = __shfl_up_sync(FULL, am.k, o);
+        ob.m = __shfl_up_sync(FULL, bb.m, o);
+        ob.k = __shfl_up_sync(FULL, bb.k, o);
+        if (lane >= o) {
+            bb = sf_add(sf_mul(ob, am), bb);
+            am = sf_mul(oa, am);
+        }
+    }
+    if (lane == 31) {
+        s_am[w] = am.m;
+        s_ak[w] = am.k;
+        s_bm[w] = bb.m;
+        s_bk[w] = bb.k;
+    }
+    Sf<V> exa, exb;
+    exa.m = __shfl_up_sync(FULL, am.m, 1);
+    exa.k = __shfl_up_sync(FULL, am.k, 1);
+    exb.m = __shfl_up_sync(FULL, bb.m, 1);
+    exb.k = __shfl_up_sync(FULL, bb.k, 1);
+    if (lane == 0) {
+        exa = Sf<V>{V(0.5), 1};
+        exb = sf_zero<V>();
+    }
+    __syncthreads();
+    if (w == 0) {
+        Sf<V> wa = (lane < NWB) ? Sf<V>{s_am[lane], s_ak[lane]} : Sf<V>{V(0.5), 1};
+        Sf<V> wb = (lane < NWB) ? Sf<V>{s_bm[lane], s_bk[lane]} : sf_zero<V>();
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Sf<V> oa, ob;
+            oa.m = __shfl_up_sync(FULL, wa.m, o);
+            oa.k = __shfl_up_sync(FULL, wa.k, o);
+            ob.m = __shfl_up_sync(FULL, wb.m, o);
+            ob.k = __shfl_up_sync(FULL, wb.k, o);
+            if (lane >= o) {
+                wb = sf_add(sf_mul(ob, wa), wb);
+                wa = sf_mul(oa, wa);
+            }
+        }
+        Sf<V> tot;
+        tot.m = __shfl_sync(FULL, wb.m, NWB - 1);
+        tot.k = __shfl_sync(FULL, wb.k, NWB - 1);
+        if (lane == 0) cagg[c] = sf_store(tot);
+        // exclusive warp prefixes (maps of the warps before)
+        Sf<V> pa, pb;
+        pa.m = __shfl_up_sync(FULL, wa.m, 1);
+        pa.k = __shfl_up_sync(FULL, wa.k, 1);
+        pb.m = __shfl_up_sync(FULL, wb.m, 1);
+        pb.k = __shfl_up_sync(FULL, wb.k, 1);
+        if (lane == 0) {
+            pa = Sf<V>{V(0.5), 1};
+            pb = sf_zero<V>();
+        }
+        __syncwarp();
+        if (lane < NWB) {
+            s_am[lane] = pa.m;
+            s_ak[lane] = pa.k;
+            s_bm[lane] = pb.m;
+            s_bk[lane] = pb.k;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(cflag + c, 1);
+        // carry into this chunk: contributions of the earlier chunks of the same instance
+        const double ws = (double)(SL * (NB + 1 - SL));
+        const double ub = chunk_base(c);
+        Sf<V> part = sf_zero<V>();
+        bool fail = false;
+        for (int p = lane; p < c; p += 32) {
+            const bool same = !a.seg || a.seg[tile_of(min(nt - 1, (p + 1) * Rc))] == a.seg[tile_of(min(nt - 1, c * Rc))];
+            if (!same) continue;
+            const int f = wait_flag(cflag + p, a.err, a.spin_limit);
+            if (f < 0) {
+                fail = true;
+                continue;
+            }
+            const double d = fabs(ub - chunk_base(p + 1));
+            part = sf_add(part, sf_scale_exp(sf_load<V>(__ldcg(cagg + p)), -ws * d));
+        }
+        if (__ballot_sync(FULL, fail) && lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+        const Sf<V> t = sf_warp_sum(part);
+        if (lane == 0) {
+            s_em = t.m;
+            s_ek = t.k;
+        }
+    }
+    __syncthreads();
+    // this thread's incoming carry: chunk carry through the maps before it
+    const Sf<V> wpa = Sf<V>{s_am[w], s_ak[w]}, wpb = Sf<V>{s_bm[w], s_bk[w]};
+    const Sf<V> chunkin = Sf<V>{s_em, s_ek};
+    Sf<V> cur = sf_add(sf_mul(sf_add(sf_mul(wpa, chunkin), wpb), exa), exb);
+    // pass 2: apply
+    for (int v = v0; v < v1; ++v) {
+        const int b = tile_of(v);
+        E[(size_t)b * NS + T] = sf_store(cur);
+        const Sf<V> dec = sf_load<V>(__ldg(pdec + (size_t)b * (NB + 1) + SL));
+        const Sf<V> o = sf_load<V>(__ldcg(own + (size_t)b * NS + T));
+        cur = sf_mul(sf_add(cur, o), dec);
     }
 }
 
@@ -1594,6 +1749,25 @@ cudaError_t launch_carry_impl(const SweepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// chunks of a level scan: at most 256 co-resident blocks over the level's states
+inline int lscan_chunks(int nt, int nstates)
+{
+    int G = 256 / (nstates > 0 ? nstates : 1);
+    G = G < 1 ? 1 : (G > 32 ? 32 : G);
+    return nt < G ? (nt > 0 ? nt : 1) : G;
+}
+
+template <int NB, typename V>
+cudaError_t launch_lscan_impl(const SweepArgs &a, cudaStream_t st, int SL, int fwd)
+{
+    int nst = 0;
+    for (int S = 1; S < (1 << NB); ++S)
+        if (popc_c(S) == SL) ++nst;
+    const dim3 grid(lscan_chunks(a.nt, nst), nst);
+    k_lscan<NB, V><<<grid, 256, 0, st>>>(a, SL, fwd);
+    return cudaGetLastError();
+}
+
 template <int NB, typename V, int NT, int C, int JCAP, int L = NB + 1>
 cudaError_t launch_bwd_impl(const SweepArgs &a, cudaStream_t st)
 {
@@ -1606,16 +1780,6 @@ cudaError_t launch_bwd_impl(const SweepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
-cudaError_t launch_fwd_impl(const SweepArgs &a, cudaStream_t st)
-{
-    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
-    auto kern = k_fwd<NB, V, NT, C, JCAP>;
-    const size_t sz = sizeof(Sm);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
-    if (e != cudaSuccess) return e;
-    kern<<<a.nt, NT, sz, st>>>(a);
-    return cudaGetLastError();
-}
+
 
 }  // namespace mmot

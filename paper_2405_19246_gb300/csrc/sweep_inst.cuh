@@ -2,6 +2,7 @@
 #pragma once
 #include "shapes.cuh"
 #include "sweep.cuh"
+#include "warp.cuh"
 
 // launchers of the three-phase design, defined for NB <= kMaxOpBits
 #define MMOT_INSTANTIATE_OPS(NB_, V_)                                                  \
@@ -25,30 +26,22 @@
     }                                                                                  \
     }
 
-#define MMOT_INSTANTIATE(NB_)                                                          \
+// launchers of the level passes and warp-tile products (l >= 6, warp.cuh)
+#define MMOT_INSTANTIATE_LEVELS(NB_, V_)                                               \
     namespace mmot {                                                                   \
     template <>                                                                        \
-    cudaError_t launch_bwd<NB_, float>(const SweepArgs &a, cudaStream_t s)             \
+    cudaError_t launch_lagg<NB_, V_>(const SweepArgs &a, cudaStream_t s, int L, int f) \
     {                                                                                  \
-        using S = Shape<NB_, float>;                                                   \
-        return launch_bwd_impl<NB_, float, S::NT, S::C, S::JCAP>(a, s);                \
+        return launch_wpass_impl<NB_, V_>(a, s, L, f);                                 \
     }                                                                                  \
     template <>                                                                        \
-    cudaError_t launch_fwd<NB_, float>(const SweepArgs &a, cudaStream_t s)             \
+    cudaError_t launch_lscan<NB_, V_>(const SweepArgs &a, cudaStream_t s, int L, int f)\
     {                                                                                  \
-        using S = Shape<NB_, float>;                                                   \
-        return launch_fwd_impl<NB_, float, S::NT, S::C, S::JCAP>(a, s);                \
+        return launch_lscan_impl<NB_, V_>(a, s, L, f);                                 \
     }                                                                                  \
     template <>                                                                        \
-    cudaError_t launch_bwd<NB_, double>(const SweepArgs &a, cudaStream_t s)            \
+    cudaError_t launch_prod<NB_, V_>(const SweepArgs &a, cudaStream_t s)               \
     {                                                                                  \
-        using S = Shape<NB_, double>;                                                  \
-        return launch_bwd_impl<NB_, double, S::NT, S::C, S::JCAP>(a, s);               \
-    }                                                                                  \
-    template <>                                                                        \
-    cudaError_t launch_fwd<NB_, double>(const SweepArgs &a, cudaStream_t s)            \
-    {                                                                                  \
-        using S = Shape<NB_, double>;                                                  \
-        return launch_fwd_impl<NB_, double, S::NT, S::C, S::JCAP>(a, s);               \
+        return launch_wprod_impl<NB_, V_>(a, s);                                       \
     }                                                                                  \
     }

@@ -1,5 +1,4 @@
 // Sweep kernels for l = 2 marginals (1 state bits).
 #include "sweep_inst.cuh"
-MMOT_INSTANTIATE(1)
 MMOT_INSTANTIATE_OPS(1, float)
 MMOT_INSTANTIATE_OPS(1, double)

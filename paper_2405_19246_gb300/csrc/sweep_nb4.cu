@@ -1,5 +1,4 @@
 // Sweep kernels for l = 5 marginals (4 state bits).
 #include "sweep_inst.cuh"
-MMOT_INSTANTIATE(4)
 MMOT_INSTANTIATE_OPS(4, float)
 MMOT_INSTANTIATE_OPS(4, double)

@@ -1,3 +1,4 @@
-// Sweep kernels for l = 7 marginals (6 state bits).
+// Level-pass and warp-tile kernels for l = 7 marginals (6 state bits).
 #include "sweep_inst.cuh"
-MMOT_INSTANTIATE(6)
+MMOT_INSTANTIATE_LEVELS(6, float)
+MMOT_INSTANTIATE_LEVELS(6, double)

@@ -1,0 +1,345 @@
+// Warp-per-tile marginal products for many state bits (l >= 6, NB >= 5).
+//
+// With 2^{l-1} >= 32 states a tile is processed by one warp: lane L holds the
+// states T = L + 32 q (q < NS/32) as scaled floats (mantissa, binary
+// exponent), and the warp walks the tile's points in order.  At a point of
+// bit k every state T containing k gains phi * F_{T\k} (Sec. 4.2 recurrences
+// grouped by subset); F_{T\k} sits in lane L ^ 2^k for k < 5 and in the same
+// lane's register q ^ 2^{k-5} otherwise, so one xor-shuffle or a register
+// select fetches it.  Every state keeps its own exponent, so states of one
+// level may differ by any factor.  Values are kept in the tile's cumulative
+// frame relative to exp(sum_{m in T} beta_m + gamma_{|T|}) (gamma_s =
+// D_1 + ... + D_s, D_r = max(0, a_r span)), as in the block engine.
+//
+// Carries: level passes (k_wpass) give each tile's own contribution to the
+// states of one level from the known lower-level carries; the scalar scans
+// of k_lscan turn them into carries.  The final kernel (k_wprod) runs the
+// backward pass of the tile from its backward carries (states at the target
+// points kept in shared memory), then the forward pass with the combine
+// M_j = sum_S F_S(x^-) G_{R\S}(x^+) and the FP64 epilogue.
+#pragma once
+#include "shapes.cuh"
+#include "sweep.cuh"
+
+namespace mmot {
+
+template <int NB, typename V>
+struct WarpRun {
+    static constexpr int NS = 1 << NB;
+    static constexpr int NQ = NS / 32;
+    static constexpr int L = NB + 1;
+    static constexpr unsigned FULL = 0xffffffffu;
+    Sf<V> f[NQ];
+    V D[NB + 1];         // D[s] = max(0, a_s span), s = 1..NB
+    double gam[NB + 1];  // gamma_s = D_1 + ... + D_s
+    V span;
+    int lane;
+
+    __device__ static constexpr int rate(int s) { return s * (L - s); }
+
+    __device__ void init(const SweepArgs &a, int b)
+    {
+        lane = threadIdx.x & 31;
+        span = (V)a.span[b];
+        gam[0] = 0.0;
+        D[0] = V(0);
+#pragma unroll
+        for (int s = 1; s <= NB; ++s) {
+            const V as = (V)(rate(s) - rate(s - 1));
+            D[s] = (as > V(0)) ? as * span : V(0);
+            gam[s] = gam[s - 1] + (double)D[s];
+        }
+    }
+
+    // sum of the baselines of the marginals in T (bits mapped around the target)
+    __device__ static double sum_beta(const double *beta, int T)
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if ((T >> k) & 1) s += beta[k];
+        return s;
+    }
+
+    // states from absolute carries (levels below maxlev; the rest 0)
+    __device__ void load_carries(const SfT<V> *carry, int b, const double *beta, int maxlev)
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int T = lane + 32 * q;
+            const int s = popc_c(T);
+            f[q] = sf_zero<V>();
+            if (T != 0 && s < maxlev)
+                f[q] = sf_scale_exp(sf_load<V>(carry[(size_t)b * NS + T]), -(sum_beta(beta, T) + gam[s]));
+        }
+    }
+
+    // Walk the tile's n points in processing order; on_target(slot, p) at the
+    // target points with the states before the point.  bits of the marginals:
+    // m < j -> m, m > j -> m - 1, target j -> -1.
+    template <typename OnT>
+    __device__ void run(const SweepArgs &a, uint32_t t0, int n, int j, bool fwd, int ntarget, OnT &&on_target)
+    {
+        const V *pos = static_cast<const V *>(a.pos);
+        const V *lphi = static_cast<const V *>(a.lphi);
+        int seen = 0;   // targets passed so far
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int r = c0 + lane;
+            V pp = V(0), lp = V(0);
+            int bit = -2;
+            if (r < n) {
+                const int id = fwd ? r : n - 1 - r;
+                const int m = a.mid[t0 + id];
+                bit = (m == j) ? -1 : (m < j ? m : m - 1);
+                const V x = pos[t0 + id];
+                pp = fwd ? x : span - x;
+                lp = lphi[t0 + id];
+            }
+            const int cnt = min(32, n - c0);
+            for (int i = 0; i < cnt; ++i) {
+                const int k = __shfl_sync(FULL, bit, i);
+                const V p = __shfl_sync(FULL, pp, i);
+                if (k == -1) {
+                    const int slot = fwd ? seen : ntarget - 1 - seen;
+                    on_target(slot, p);
+                    ++seen;
+                    continue;
+                }
+                const V l = __shfl_sync(FULL, lp, i);
+                // injection factor of level lane+1 in lane lane (level s = |T|)
+                V facl = V(0);
+                if (lane < NB) {
+                    const int s = lane + 1;
+                    facl = vexp<V>(l + (V)(rate(s) - rate(s - 1)) * p - D[s]);
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int T = lane + 32 * q;
+                    const V fac = __shfl_sync(FULL, facl, (popc_c(T) + 31) & 31);
+                    Sf<V> src;
+                    if (k < 5) {
+                        src.m = __shfl_xor_sync(FULL, f[q].m, 1 << k);
+                        src.k = __shfl_xor_sync(FULL, f[q].k, 1 << k);
+                    } else {
+                        src = f[0];
+#pragma unroll
+                        for (int q2 = 0; q2 < NQ; ++q2)
+                            if (q2 == (q ^ (1 << (k - 5)))) src = f[q2];
+                    }
+                    if ((T >> k) & 1) {
+                        // F_{T\k}, with the empty state equal to 1
+                        if ((T ^ (1 << k)) == 0) src = Sf<V>{V(0.5), 1};
+                        if (src.m != V(0)) {
+                            Sf<V> t = sf_make<V>(src.m * fac);
+                            t.k += src.k;
+                            if (t.m != V(0)) f[q] = sf_add(f[q], t);
+                        }
+                    }
+                }
+            }
+        }
+    }
+};
+
+// number of target points of the tile
+__device__ __forceinline__ int warp_count_targets(const SweepArgs &a, uint32_t t0, int n, int j)
+{
+    int c = 0;
+    for (int r = threadIdx.x & 31; r < n; r += 32) c += (a.mid[t0 + r] == j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    return c;
+}
+
+__device__ __forceinline__ void warp_betas(const SweepArgs &a, int b, int j, int NB, double *beta)
+{
+    for (int k = 0; k < NB; ++k) {
+        const int m = (k < j) ? k : k + 1;
+        const int rt = __ldg(a.reftile + (size_t)b * a.l + m);
+        beta[k] = *(volatile const double *)(a.beta + (size_t)rt * a.l + m);
+    }
+}
+
+// Level pass: the tile's own contribution to the states of level SL at its
+// base, from the carries of the lower levels.  4 warps per block, one tile
+// per warp.
+template <int NB, typename V>
+__global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
+{
+    constexpr int NS = 1 << NB;
+    const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (b >= a.nt) return;
+    if (a.frozen && (a.mode == MODE_UPDATE || a.mode == MODE_RESIDUAL) && a.frozen[a.seg[b]]) return;
+    const bool fwd = (fwd_i != 0);
+    const uint32_t t0 = a.tstart[b];
+    const int n = (int)(a.tstart[b + 1] - t0);
+    double beta[NB];
+    warp_betas(a, b, a.j, NB, beta);
+    WarpRun<NB, V> r;
+    r.init(a, b);
+    r.load_carries(sfp<V>(fwd ? a.fcarry : a.bcarry), b, beta, SL);
+    r.run(a, t0, n, a.j, fwd, 0, [](int, V) {});
+#pragma unroll
+    for (int q = 0; q < WarpRun<NB, V>::NQ; ++q) {
+        const int T = r.lane + 32 * q;
+        if (popc_c(T) == SL)
+            sfp<V>(a.agg)[(size_t)b * NS + T] =
+                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V>::sum_beta(beta, T) + r.gam[SL]));
+    }
+}
+
+// One tile of a marginal product (both carries known): backward pass with the
+// states at the target points in shared memory, forward pass with the
+// combine, FP64 epilogue.  One warp per block (shared memory holds the
+// backward states of up to JCAP targets).
+template <int NB, typename V>
+__global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
+{
+    using R = WarpRun<NB, V>;
+    constexpr int NS = 1 << NB;
+    constexpr int NQ = R::NQ;
+    constexpr int JCAP = WShape<NB, V>::JCAP;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ SfT<V> Gt[JCAP * NS];
+    __shared__ double gq[JCAP];
+    const int b = blockIdx.x;
+    if (a.frozen && (a.mode == MODE_UPDATE || a.mode == MODE_RESIDUAL) && a.frozen[a.seg[b]]) {
+        if (a.mode == MODE_RESIDUAL && threadIdx.x == 0) a.partial[b] = 0.0;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const uint32_t t0 = a.tstart[b];
+    const int n = (int)(a.tstart[b + 1] - t0);
+    const int nt = warp_count_targets(a, t0, n, a.j);
+    if (nt > JCAP) {
+        if (lane == 0) atomicOr(a.err, ERR_RANGE);
+        return;
+    }
+    double beta[NB];
+    warp_betas(a, b, a.j, NB, beta);
+    double sb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) sb += beta[k];
+    const double eps_b = tile_eps(a, b);
+    const double inv_eps_b = a.teps ? 1.0 / eps_b : a.inv_eps;
+
+    // backward states at the target points
+    R rb;
+    rb.init(a, b);
+    rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
+    rb.run(a, t0, n, a.j, false, nt, [&](int slot, V) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) Gt[slot * NS + lane + 32 * q] = sf_store(rb.f[q]);
+    });
+    __syncwarp();
+
+    // forward pass and combine: ln M = sb + E ln 2 + ln(sum), per target
+    R rf;
+    rf.init(a, b);
+    rf.load_carries(sfp<V>(a.fcarry), b, beta, NB + 1);
+    const int32_t off = a.cnt[(size_t)b * a.l + a.j];
+    V qmax = V(-INFINITY);
+    bool bad = false;
+    double racc = 0.0;
+    rf.run(a, t0, n, a.j, true, nt, [&](int slot, V pF) {
+        const V pG = rb.span - pF;
+        // per-level factor exp(gamma^F_s + gamma^G_{NB-s} - w_s pF - w_{NB-s} pG)
+        // as 2^(n_s) * mu_s, computed by lane s
+        int en = 0;
+        V em = V(0);
+        if (lane <= NB) {
+            const int s = lane;
+            const double c = (rf.gam[s] + rb.gam[NB - s] - (double)R::rate(s) * (double)pF -
+                              (double)R::rate(NB - s) * (double)pG) * kLog2e;
+            const double fl = floor(c);
+            en = (int)fl;
+            em = vexp2<V>((V)(c - fl));
+        }
+        int Emax = INT_MIN / 2;
+        V sum = V(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int S = lane + 32 * q;
+            const int s = popc_c(S);
+            const int ens = __shfl_sync(FULL, en, s);
+            const V ems = __shfl_sync(FULL, em, s);
+            const Sf<V> fS = (S == 0) ? Sf<V>{V(0.5), 1} : rf.f[q];
+            const int U = (NS - 1) ^ S;
+            const Sf<V> gU = (U == 0) ? Sf<V>{V(0.5), 1} : sf_load<V>(Gt[slot * NS + U]);
+            if (fS.m != V(0) && gU.m != V(0)) {
+                const Sf<V> z = sf_make<V>(fS.m * gU.m * ems);
+                const int E = z.k + fS.k + gU.k + ens;
+                if (E > Emax) {
+                    sum = fma(sum, pow2neg<V>(Emax - E), z.m);
+                    Emax = E;
+                } else {
+                    sum = fma(z.m, pow2neg<V>(E - Emax), sum);
+                }
+            }
+        }
+        // across the warp
+        int Ew = Emax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Ew = max(Ew, __shfl_xor_sync(FULL, Ew, o));
+        V sw = (sum > V(0)) ? sum * pow2neg<V>(Emax - Ew) : V(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULL, sw, o);
+        const double lnM = (sw > V(0)) ? sb + (double)Ew * kLn2 + (double)vlog<V>(sw) : -INFINITY;
+        if (lane == 0) {
+            const int i = off + slot;
+            if (a.mode == MODE_UPDATE) {
+                const double lm = a.lnmuj[i];
+                double g = -INFINITY;
+                if (lm > -INFINITY) {
+                    g = lm - lnM;
+                    if (!isfinite(g)) bad = true;
+                    qmax = fmax(qmax, (V)g);
+                }
+                gq[slot] = g;
+            } else if (a.mode == MODE_RESIDUAL) {
+                const double gg = a.gj[i];
+                const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
+                racc += fabs(marg - a.muj[i]);
+            } else if (a.mode == MODE_OUT_M) {
+                a.out[i] = (lnM == -INFINITY) ? 0.0 : exp(lnM);
+            } else if (a.mode == MODE_OUT_PLAN) {
+                a.out[i] = (a.gj[i] == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(a.gj[i] * inv_eps_b + lnM);
+            } else {
+                a.out[i] = lnM;
+            }
+        }
+    });
+    if (lane == 0) {
+        if (a.mode == MODE_UPDATE) {
+            if (bad) atomicOr(a.err, ERR_NONFINITE);
+            const double bx = isfinite((double)qmax) ? (double)qmax : 0.0;
+            if (nt > 0) a.beta[(size_t)b * a.l + a.j] = bx;
+            V *lph = static_cast<V *>(a.lphi);
+            for (int slot = 0, r = 0; r < n; ++r) {
+                if (a.mid[t0 + r] != a.j) continue;
+                const double g = gq[slot];
+                a.gj[off + slot] = eps_b * g;
+                lph[t0 + r] = (V)(g - bx);
+                ++slot;
+            }
+        } else if (a.mode == MODE_RESIDUAL) {
+            a.partial[b] = racc;
+        }
+    }
+}
+
+template <int NB, typename V>
+cudaError_t launch_wpass_impl(const SweepArgs &a, cudaStream_t st, int SL, int fwd)
+{
+    k_wpass<NB, V><<<(a.nt + 3) / 4, 128, 0, st>>>(a, SL, fwd);
+    return cudaGetLastError();
+}
+
+template <int NB, typename V>
+cudaError_t launch_wprod_impl(const SweepArgs &a, cudaStream_t st)
+{
+    k_wprod<NB, V><<<a.nt, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mmot

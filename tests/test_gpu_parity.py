@@ -88,8 +88,11 @@ def test_sparse_supports_small_eps(Plan, prec, l, N, eps, inst):
         for j in range(l):
             ref = oracle.marginal_subset(xs, gs, eps, j)
             got = plan.marginal(j, "lnM")
-            # a log value of magnitude L carries a rounding error of order u L
+            # a log value of magnitude L carries a rounding error of order u L;
+            # decay exponents reach w_max x/eps (w_max = floor(l/2) ceil(l/2))
             tol = TOL[prec] * max(1.0, 1e-2 * float(np.max(np.abs(ref))))
+            if prec == "fp64":
+                tol += 8 * 1.1e-16 * (l // 2) * ((l + 1) // 2) * max(float(np.max(x)) for x in xs) / eps
             assert _lnM_err(got, ref) <= tol, (it, j, _lnM_err(got, ref))
             gs[j] = oracle.potential_update(mus[j], ref, eps)
             plan.set_potentials(j, gs[j])
