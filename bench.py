@@ -229,16 +229,170 @@ def oracle_iteration_sample(w, xs, mus):
     return (n_prod / w["l"]) / dt, dt, n_prod
 
 
+def batched_instances(count, seed_offset=0):
+    """The batched workload's instances: (l, N, eps) drawn from the batched
+    configuration, inputs from the seeded generators."""
+    from paper_2405_19246_gb300 import workloads as wl
+    params = wl.batched_instance_params(4096 + seed_offset)[seed_offset:seed_offset + count]
+    return params, [(*wl.batched_instance(i + seed_offset, l, N), e) for i, (l, N, e) in enumerate(params)]
+
+
+def fp64_one_at_a_time(inst, tol, itr_max, limit_s):
+    """Plain single-instance FP64 GPU solves, one after another: seconds per
+    solve for as many instances as fit in limit_s."""
+    import torch
+    from paper_2405_19246_gb300.api import Plan
+    times, conv = [], 0
+    t_all = time.perf_counter()
+    for xs, mus, eps in inst:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with Plan(xs, mus, eps, precision="fp64") as P:
+            it, res = 0, float("inf")
+            while it < itr_max and res > tol and time.perf_counter() - t_all < limit_s:
+                res = P.sinkhorn_step(min(20, itr_max - it), residual=True)
+                it += min(20, itr_max - it)
+        torch.cuda.synchronize()
+        if it < itr_max and res > tol:
+            break   # time limit reached inside this solve: not counted
+        times.append(time.perf_counter() - t0)
+        conv += int(res <= tol)
+        if time.perf_counter() - t_all > limit_s:
+            break
+    return times, conv
+
+
+def run_batched(args):
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_2405_19246_gb300.api import Batch
+    from paper_2405_19246_gb300.autotune import tune_tile_points
+    params, inst = batched_instances(args.instances)
+    points = sum(l * N for l, N, e in params)
+    torch.cuda.init()
+    tp, tune = tune_tile_points(inst, precision=args.precision, sample=min(32, len(inst)))
+    t0 = time.perf_counter()
+    B = Batch(inst, precision=args.precision, tile_points=tp)
+    create_s = time.perf_counter() - t0
+    info = B.info()
+    for _ in range(args.warmup):
+        B.reset()
+        B.step(args.check_every, args.tol)
+    torch.cuda.synchronize()
+    ms = 0.0
+    res = None
+    launches0 = B.info()["kernel_launches"]
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = B.solve(args.tol, args.itr_max, check_every=args.check_every, results=False)
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    st = [B.status(i) for i in range(len(inst))]
+    launches = B.info()["kernel_launches"] - launches0
+    B.close()
+    conv = sum(s["converged"] for s in st)
+    inst_iters = sum(s["iters"] if s["converged"] else args.itr_max for s in st)
+    value = len(inst) * args.steps / (ms / 1000.0)
+    base_t, base_conv = fp64_one_at_a_time(inst[:16], args.tol, args.itr_max, 120.0)
+    line = {"metric": "batched solves/s", "value": value, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched: %d instances drawn from l uniform in {3..8}, N log-uniform "
+                                   "[64, 65536], eps log-uniform [1e-3, 1e-1], sorted U[0,1] supports, "
+                                   "LogNormal(0,1) weights; stop at residual %.0e or %d iterations"
+                                   % (len(inst), args.tol, args.itr_max),
+                       "instances": len(inst), "points": points, "tol": args.tol, "itr_max": args.itr_max,
+                       "check_every": args.check_every, "tile_points": tp, "groups": info["groups"],
+                       "tiles": info["tiles"]},
+            "autotune_s_per_iter": {str(k): v for k, v in tune.items()},
+            "converged": conv, "instance_iterations_per_s": inst_iters * args.steps / (ms / 1000.0),
+            "e2e": {"value": len(inst) / (ms / 1000.0 / args.steps + create_s), "unit": "solves/s",
+                    "h2d_bytes_per_step": sum(x.nbytes + m.nbytes for xs, mus, e in inst for x, m in zip(xs, mus)),
+                    "d2h_bytes_per_step": 8 * len(inst), "includes": "batch creation from host arrays"},
+            "gpu_launches": launches,
+            "fp64_one_at_a_time": {"solves": len(base_t), "converged": base_conv,
+                                   "solves_per_s": len(base_t) / sum(base_t) if base_t else None,
+                                   "sample": "the first %d instances of the batch, sequential" % len(base_t)}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_2405_19246_gb300 import workloads as wl
+    from paper_2405_19246_gb300.serve import Request, Server, latency_stats
+    rng = np.random.default_rng(5)
+    n = max(1, int(round(args.rate * args.duration)))
+    t = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
+    params, inst = batched_instances(n, seed_offset=8192)
+    arrivals = []
+    for i, (ti, (xs, mus, eps)) in enumerate(zip(t, inst)):
+        if rng.random() < 0.01:   # 1% large requests: l = 6, N = 2^20
+            xs, mus = wl.sorted_uniform_lognormal(l=6, N=1 << 20, seed_cfg=wl.CFG_SERVING, instance=i)
+        arrivals.append((float(ti), Request(rid=i, xs=xs, mus=mus, eps=eps)))
+    torch.cuda.init()
+    srv = Server(precision=args.precision, tol=args.tol, itr_max=args.itr_max, check_every=args.check_every,
+                 mem_budget=int(args.mem_gb * (1 << 30)))
+    t0 = time.perf_counter()
+    done = srv.run(arrivals)
+    wall = time.perf_counter() - t0
+    st = latency_stats(done)
+    # the same arrivals served one at a time by plain FP64 solves (FIFO), from
+    # measured service times of a sample
+    svc, _ = fp64_one_at_a_time([(r.xs, r.mus, r.eps) for _, r in arrivals[:8]], args.tol, args.itr_max, 60.0)
+    clock, lat = 0.0, []
+    for k, (ta, _) in enumerate(arrivals):
+        clock = max(clock, ta) + svc[k % len(svc)]
+        lat.append(clock - ta)
+    line = {"metric": "served solves/s", "value": len(done) / wall, "unit": "solves/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": wall * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals at %g req/s for %g s, instances as in the "
+                                   "batched configuration plus 1%% large (l=6, N=2^20); stop at residual "
+                                   "%.0e or %d iterations" % (args.rate, args.duration, args.tol, args.itr_max),
+                       "requests": n, "rate": args.rate, "mem_budget_gb": args.mem_gb,
+                       "check_every": args.check_every, "cohorts": srv.admissions},
+            "latency": st,
+            "fp64_one_at_a_time": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                                   "solves_per_s": n / clock if clock > 0 else None,
+                                   "service_sample_s": svc,
+                                   "model": "FIFO queue, service times of the first %d requests cycled" % len(svc)}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--instances", type=int, default=64, help="batched: instances")
+    ap.add_argument("--tol", type=float, default=1e-6, help="batched/serving: residual to stop at")
+    ap.add_argument("--itr-max", type=int, default=1000, help="batched/serving: iteration budget")
+    ap.add_argument("--check-every", type=int, default=20)
+    ap.add_argument("--rate", type=float, default=1000.0, help="serving: requests per second")
+    ap.add_argument("--duration", type=float, default=0.1, help="serving: seconds of arrivals")
+    ap.add_argument("--mem-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batched" and args.impl == "ours":
+        return run_batched(args)
+    if args.workload == "serving" and args.impl == "ours":
+        return run_serving(args)
+    if args.workload in ("batched", "serving"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no batched or served mode"}))
+        return 0
     w = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -238,6 +238,10 @@ mmot_status mmot_batch_reset(mmot_batch b);
  * instance did not converge. */
 mmot_status mmot_batch_solve(mmot_batch b, double tol, int itr_max, int check_every, mmot_result *results);
 
+/* Freeze instance i (no further updates), e.g. when a caller's iteration
+ * budget for it is spent; its status keeps converged = 0. */
+mmot_status mmot_batch_freeze(mmot_batch b, int i);
+
 /* Iterations run, last checked residual and converged flag of instance i. */
 mmot_status mmot_batch_status(mmot_batch b, int i, int *iters, double *residual, int *converged);
 

@@ -30,7 +30,7 @@ EXPORTED = [
     "mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve", "mmot_objective",
     "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
     "mmot_get_profile", "mmot_get_info", "mmot_marginal_noalloc",
-    "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_status",
+    "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_freeze", "mmot_batch_status",
     "mmot_batch_get_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
     "mmot_destroy", "mmot_last_error",
 ]
@@ -89,6 +89,7 @@ def lib():
         L.mmot_batch_step.argtypes = [vp, i, d, P(i)]
         L.mmot_batch_reset.argtypes = [vp]
         L.mmot_batch_solve.argtypes = [vp, d, i, i, P(MmotResult)]
+        L.mmot_batch_freeze.argtypes = [vp, i]
         L.mmot_batch_status.argtypes = [vp, i, P(i), P(d), P(i)]
         L.mmot_batch_get_potentials.argtypes = [vp, i, i, vp]
         L.mmot_batch_get_info.argtypes = [vp, P(MmotBatchInfo)]

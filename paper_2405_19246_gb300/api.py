@@ -237,6 +237,10 @@ class Batch:
         return [dict(iters=r.iters, residual=r.residual, W=r.W, primal=r.primal, dual=r.dual,
                      mass=r.mass) for r in arr]
 
+    def freeze(self, i):
+        """Stop updating instance i (its iteration budget is spent)."""
+        nat.check(nat.lib().mmot_batch_freeze(self._h, int(i)))
+
     def status(self, i):
         it, res, cv = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
         nat.check(nat.lib().mmot_batch_status(self._h, int(i), ctypes.byref(it), ctypes.byref(res),

@@ -1238,6 +1238,7 @@ struct mmot_batch_s {
         std::vector<int> iters;       // iterations when found converged (else run so far)
         std::vector<double> res;      // last checked residual
         std::vector<int32_t> conv;    // converged (frozen)
+        std::vector<int32_t> frozen_only;   // frozen by the caller without converging
         int done = 0;                 // iterations run on the group
         int active = 0;
     };
@@ -1271,7 +1272,7 @@ mmot_status group_check(mmot_batch_s::Group &G, double tol)
     int active = 0;
     bool changed = false;
     for (int q = 0; q < ns; ++q) {
-        if (G.conv[q]) continue;
+        if (G.conv[q] || G.frozen_only[q]) continue;
         G.res[q] = r[q];
         G.iters[q] = G.done;
         if (r[q] <= tol) {
@@ -1282,8 +1283,12 @@ mmot_status group_check(mmot_batch_s::Group &G, double tol)
         }
     }
     G.active = active;
-    if (changed)
-        CUDA_TRY(cudaMemcpyAsync(p->d_frozen, G.conv.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, p->st));
+    if (changed) {
+        std::vector<int32_t> fz(ns);
+        for (int q = 0; q < ns; ++q) fz[q] = G.conv[q] | G.frozen_only[q];
+        CUDA_TRY(cudaMemcpyAsync(p->d_frozen, fz.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, p->st));
+        CUDA_TRY(cudaStreamSynchronize(p->st));
+    }
     return check_device_error(p);
 }
 
@@ -1295,6 +1300,7 @@ mmot_status group_reset(mmot_batch_s::Group &G)
     G.iters.assign(ns, 0);
     G.res.assign(ns, INFINITY);
     G.conv.assign(ns, 0);
+    G.frozen_only.assign(ns, 0);
     G.done = 0;
     G.active = ns;
     return MMOT_OK;
@@ -1444,6 +1450,21 @@ mmot_status mmot_batch_solve(mmot_batch b, double tol, int itr_max, int check_ev
     for (auto &G : b->groups)
         if (G.active > 0) return fail(MMOT_ERR_NOT_CONVERGED, "%d instance(s) with l = %d above tol after %d iterations",
                                       G.active, G.l, t);
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_freeze(mmot_batch b, int i)
+{
+    if (!b) return fail(MMOT_ERR_INVALID_ARG, "NULL batch");
+    if (i < 0 || i >= b->n) return fail(MMOT_ERR_INVALID_ARG, "instance %d out of range", i);
+    auto &G = b->groups[b->where[i].first];
+    const int q = b->where[i].second;
+    if (G.frozen_only[q] || G.conv[q]) return MMOT_OK;
+    G.frozen_only[q] = 1;
+    G.active -= 1;
+    const int32_t one = 1;
+    CUDA_TRY(cudaMemcpyAsync(G.p->d_frozen + q, &one, sizeof(int32_t), cudaMemcpyHostToDevice, G.p->st));
+    CUDA_TRY(cudaStreamSynchronize(G.p->st));
     return MMOT_OK;
 }
 

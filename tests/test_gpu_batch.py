@@ -125,3 +125,25 @@ def test_instance_result_is_independent_of_its_neighbours(api):
         for k in range(len(xs)):
             d = np.max(np.abs(A.get_potentials(3, k) - B.get_potentials(5, k))) / eps
             assert d <= TOL_G["fp32"], (k, d)
+
+
+def test_served_result_same_alone_and_in_mix(api):
+    """A request served alone and the same request served among others
+    (other cohorts overlapping on the device) give the same result."""
+    from paper_2405_19246_gb300.serve import Request, Server
+    inst = _mixed_instances(10, seed=907, N_range=(40, 400), eps_range=(3e-2, 1e-1), l_range=(3, 7))
+
+    def req(i):
+        xs, mus, eps = inst[i]
+        return Request(rid=i, xs=xs, mus=mus, eps=eps)
+
+    alone = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True).run([(0.0, req(4))])
+    mix = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True, max_cohort=3)
+    res = {r.rid: r for r in mix.run([(0.005 * i, req(i)) for i in range(10)])}
+    a, m = alone[0], res[4]
+    assert len(res) == 10 and mix.admissions >= 2
+    assert a.converged and m.converged and a.iters == m.iters
+    eps = inst[4][2]
+    for k in range(len(inst[4][0])):
+        d = np.max(np.abs(a.potentials[k] - m.potentials[k])) / eps
+        assert d <= 2e-4, (k, d)

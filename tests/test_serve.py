@@ -1,0 +1,100 @@
+"""Host logic of the continuous-batching server (no GPU): admission by
+memory budget in arrival order, cohort retirement, iteration budgets and
+latency bookkeeping, with a stand-in for the device batch."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2405_19246_gb300.serve import Request, Server, estimate_bytes, latency_stats
+
+
+class FakeBatch:
+    """Instance i converges after need[i] iterations (residual 1/(1+iters))."""
+
+    live = 0
+    peak = 0
+    lock = threading.Lock()
+
+    def __init__(self, reqs, need):
+        self.reqs = reqs
+        self.need = [need[r.rid] for r in reqs]
+        self.it = 0
+        self.frozen = [False] * len(reqs)
+        self.conv = [False] * len(reqs)
+        self.conv_it = [0] * len(reqs)
+        with FakeBatch.lock:
+            FakeBatch.live += 1
+            FakeBatch.peak = max(FakeBatch.peak, FakeBatch.live)
+
+    def step(self, n, tol):
+        time.sleep(0.001)
+        self.it += n
+        for i, nd in enumerate(self.need):
+            if not self.conv[i] and not self.frozen[i] and self.it >= nd:
+                self.conv[i] = True
+                self.conv_it[i] = self.it
+        return sum(not (c or f) for c, f in zip(self.conv, self.frozen))
+
+    def status(self, i):
+        it = self.conv_it[i] if self.conv[i] else self.it
+        return dict(iters=it, residual=1.0 / (1 + it), converged=self.conv[i])
+
+    def freeze(self, i):
+        self.frozen[i] = True
+
+    def get_potentials(self, i, k):
+        return np.full(3, float(self.reqs[i].rid))
+
+    def close(self):
+        with FakeBatch.lock:
+            FakeBatch.live -= 1
+
+
+def _reqs(n, N=100, l=3):
+    return [Request(rid=i, xs=[np.zeros(N)] * l, mus=[np.zeros(N)] * l, eps=0.1) for i in range(n)]
+
+
+def test_all_requests_finish_in_budget_and_order():
+    reqs = _reqs(40)
+    need = {r.rid: 20 * (1 + r.rid % 5) for r in reqs}
+    FakeBatch.peak = 0
+    per = estimate_bytes(reqs[0])
+    srv = Server(check_every=10, itr_max=1000, mem_budget=4 * per, max_cohort=3,
+                 make_batch=lambda rs: FakeBatch(rs, need), keep_potentials=True)
+    arrivals = [(0.0005 * i, r) for i, r in enumerate(reqs)]
+    done = srv.run(arrivals)
+    assert len(done) == 40 and all(r.converged for r in done)
+    # a cohort holds at most 3 requests and at most 4 requests' memory runs at once
+    assert srv.admissions >= 14
+    assert FakeBatch.peak <= 4
+    # admission follows arrival order
+    adm = sorted(reqs, key=lambda r: r.admitted)
+    assert [r.rid for r in adm] == sorted(r.rid for r in adm)
+    # each result belongs to its request; iterations are the ones that converged it
+    for r in done:
+        assert r.potentials[0][0] == r.rid
+        assert r.iters == need[r.rid]
+        assert r.finished >= r.admitted >= r.arrival
+
+
+def test_iteration_budget_ends_unconverged_requests():
+    reqs = _reqs(6)
+    need = {r.rid: (30 if r.rid % 2 else 10 ** 9) for r in reqs}
+    srv = Server(check_every=10, itr_max=50, make_batch=lambda rs: FakeBatch(rs, need))
+    done = srv.run([(0.0, r) for r in reqs])
+    assert len(done) == 6
+    for r in done:
+        assert r.converged == bool(r.rid % 2)
+        assert r.iters == (30 if r.rid % 2 else 50)
+    st = latency_stats(done)
+    assert st["count"] == 6 and st["converged"] == 3 and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_oversized_request_runs_alone():
+    reqs = _reqs(3, N=10 ** 6, l=6)
+    need = {r.rid: 10 for r in reqs}
+    FakeBatch.peak = 0
+    srv = Server(check_every=10, mem_budget=1, make_batch=lambda rs: FakeBatch(rs, need))
+    done = srv.run([(0.0, r) for r in reqs])
+    assert len(done) == 3 and FakeBatch.peak == 1
