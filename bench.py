@@ -190,11 +190,12 @@ def run_ours(args, w, rank, world, local_rank):
         torch.distributed.barrier()
 
     # per-kernel timing of the same launches with CUDA events on the plan stream
+    n_prof = min(20, w["iters"])
     plan.reset_potentials()
-    plan.sinkhorn_step(20)
+    plan.sinkhorn_step(n_prof)
     plan.profile(True)
     plan.profile_stats(reset=True)
-    plan.sinkhorn_step(20)
+    plan.sinkhorn_step(n_prof)
     stats = plan.profile_stats(reset=True)
     plan.profile(False)
 
@@ -456,11 +457,12 @@ def main():
     stream = T * (2 * esz + 1)           # position, ln phi (esz B each) and marginal id
     target_io = w["N"] * (16 + esz)      # ln mu read, g write, ln phi write at the N_j targets
     kbytes = {"k_fwd": stream + target_io, "k_prod": stream + target_io, "k_bwd": stream,
-              "k_tileop": stream, "k_carry": None}
+              "k_tileop": stream, "k_carry": None, "k_wprod": stream + target_io,
+              "k_wpass": stream, "k_lscan": None}
     dom = max(stats, key=lambda k: stats[k][1])
     n_dom, ms_dom = stats[dom]
     avg = ms_dom / max(1, n_dom) / 1000.0
-    bytes_dom = kbytes[dom]
+    bytes_dom = kbytes.get(dom)
     achieved = bytes_dom / avg / 1e9 if (avg > 0 and bytes_dom) else None
     src_hash = kernel_source_hash()
     traffic = NCU_TRAFFIC.get((args.workload, args.precision, dom, src_hash))

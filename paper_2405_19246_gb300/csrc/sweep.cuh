@@ -478,6 +478,36 @@ struct Engine {
         }
     }
 
+    // Branch-free injection of point c (few states): every state T takes the
+    // value of T\k for the point's bit k through a select, so the lanes of a
+    // warp, whose points belong to different marginals, do not diverge.  A
+    // state not containing k selects 0; T\k never contains k, so it is not
+    // changed by this point and the in-place update is exact.
+    template <int SMAX>
+    __device__ __forceinline__ void inject_select(int c, int k)
+    {
+        V fu[NS];
+        fu[0] = V(1);
+        static_for<1, NS>([&](auto uc) {
+            constexpr int U = decltype(uc)::value;
+            if constexpr (popc_c(U) < SMAX) fu[U] = carry[U] + run[U];
+        });
+        static_for<1, NS>([&](auto tc) {
+            constexpr int T = decltype(tc)::value;
+            if constexpr (popc_c(T) <= SMAX) {
+                V src = V(0);
+                static_for<0, NB>([&](auto kc) {
+                    constexpr int KB = decltype(kc)::value;
+                    if constexpr ((T >> KB) & 1) {
+                        constexpr int U = T ^ (1 << KB);
+                        src = (k == KB) ? fu[U] * ratio<T, KB>() : src;
+                    }
+                });
+                run[T] = fma(fac[c][popc_c(T) - 1], src, run[T]);
+            }
+        });
+    }
+
     // Walk the chunk, recomputing levels 1..SMAX; on_target(c) is called at
     // target points with run[] holding the local sums before the point.
     template <int SMAX, typename OnT>
@@ -489,10 +519,15 @@ struct Engine {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int k = bit[c];
-            if (k >= 0)
-                inject_dispatch<SMAX>(k, c);
-            else if (k == -1)
-                on_target(c);
+            if constexpr (RREG) {
+                inject_select<SMAX>(c, k);
+                if (k == -1) on_target(c);
+            } else {
+                if (k >= 0)
+                    inject_dispatch<SMAX>(k, c);
+                else if (k == -1)
+                    on_target(c);
+            }
         }
     }
 
