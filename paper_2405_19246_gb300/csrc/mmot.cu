@@ -691,7 +691,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     if (l - 1 > kMaxOpBits) {
         // warp-tile products (warp.cuh)
         K = fp64 ? wshape_k<double>(l - 1) : wshape_k<float>(l - 1);
-        jcap = K / 2;
+        jcap = K / 4;   // WShape<NB, V>::JCAP
     }
     if (tile_points > 0) K = std::max(32, std::min(K, tile_points));
     const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;

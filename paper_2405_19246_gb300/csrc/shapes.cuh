@@ -43,11 +43,13 @@ MMOT_SHAPE(7, double, 64, 1)
 #undef MMOT_SHAPE
 
 // points per warp tile of the products with l >= 6 (warp.cuh; the plan's
-// tiling uses at most this many, half of them of one marginal)
+// tiling uses at most this many, a quarter of them of one marginal: with
+// l >= 6 marginals a tile holds about K/l points of each, and the backward
+// states kept per target (2^{l-1} scaled floats) set the shared memory)
 template <int NB, typename V>
 struct WShape {
     static constexpr int K = (sizeof(V) == 4) ? (NB <= 5 ? 128 : 64) : (NB <= 5 ? 64 : 32);
-    static constexpr int JCAP = K / 2;
+    static constexpr int JCAP = K / 4;
 };
 
 constexpr double kSpanLimitF32 = 24.0;

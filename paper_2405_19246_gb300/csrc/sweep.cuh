@@ -1051,13 +1051,28 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
     // per-tile constants of the combine: binary exponent of the product of the
     // two states' scales, and the FP64 base
     __shared__ double s_base;
+    __shared__ int s_emax, s_fast;
+    __shared__ V s_sc[NS];
     for (int S = tid; S < NS; S += NT) sm.eS[S] = (sm.Gs[S].k - 1) + (sm.GsG[FULLS ^ S].k - 1);
+    __syncthreads();
     if (tid == 0) {
         double sb = 0.0;
         for (int k = 0; k < NB; ++k) sb += sm.beta[k];
         s_base = sb;
+        int emx = INT_MIN, emn = INT_MAX;
+        for (int S = 0; S < NS; ++S) {
+            emx = max(emx, sm.eS[S]);
+            emn = min(emn, sm.eS[S]);
+        }
+        s_emax = emx;
+        // fast combine when the states' scales lie within 2^60 of each other
+        s_fast = (emx - emn <= 60) ? 1 : 0;
     }
     __syncthreads();
+    for (int S = tid; S < NS; S += NT) s_sc[S] = pow2neg<V>(sm.eS[S] - s_emax);
+    __syncthreads();
+    const bool fast = (s_fast != 0);
+    const int emax_t = s_emax;
     // ln M = base + xE ln 2 + xM: per-tile FP64 base, the binary exponent of
     // the largest term and a small in-tile part.  Every term F_S G_{R\S} is
     // formed as mantissa x 2^exponent, so terms whose states carry very
@@ -1079,7 +1094,21 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
         for (int s = 0; s <= NB; ++s) q[s] = vexp<V>(-(En::rate(s) * pF + En::rate(NB - s) * pG));
         int Emax = INT_MIN / 2;
         V sum = V(0);
-        if (sl < JCAP) {
+        if (fast && sl < JCAP) {
+            // plain products relative to the tile's largest state scale: a sum
+            // above 2^-100 means every term that matters was formed exactly
+#pragma unroll(En::UNR)
+            for (int S = 0; S < NS; ++S) {
+                const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
+                sum = fma(fS * sm.G[(FULLS ^ S) * JCAP + sl], s_sc[S] * q[popc_c(S)], sum);
+            }
+            if (sum >= pow2neg<V>(-100)) {
+                Emax = emax_t;
+            } else {
+                sum = V(0);
+            }
+        }
+        if (sum == V(0) && sl < JCAP) {
 #pragma unroll(En::UNR)
             for (int S = 0; S < NS; ++S) {
                 const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
