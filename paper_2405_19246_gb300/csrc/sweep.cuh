@@ -35,6 +35,7 @@
 #pragma once
 #include <limits>
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
@@ -332,7 +333,8 @@ struct SweepSmem {
     // composition (NB x NS x NT values)
     static constexpr int OPSZ = (NB <= kMaxOpBits) ? NB * NS * (NT / 32) : 0;
     static constexpr int GSZ = (NS * JCAP > OPSZ) ? NS * JCAP : OPSZ;
-    V G[WITH_G ? GSZ : 1];
+    // 16-byte aligned: the epilogue keeps FP64 values in this space
+    alignas(16) V G[WITH_G ? GSZ : 1];
     double lmu[WITH_G ? JCAP : 1];   // ln mu of the tile's target points (prefetched)
 };
 
@@ -1133,75 +1135,93 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
     // ---- FP64 epilogue ------------------------------------------------------
     const int32_t off = off0;
     __pipeline_wait_prior(0);
-    __syncthreads();
-    if (a.mode == MODE_UPDATE) {
-        // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base) - xM   (FP64)
-        double gq[C];
-        V qmax = V(-INFINITY);   // new baseline: the tile maximum of g_j/eps
-        bool bad = false;
+    __syncthreads();   // the combine no longer reads sm.G
+    if constexpr (NB >= 2) {
+        // by target slot instead of by chunk position: the FP64 work of a
+        // target runs once, not once per chunk step of a warp whose lanes hold
+        // targets at different steps.  Per slot xM, xE and g/eps live in the
+        // space of the backward states.
+        using SmT = SweepSmem<NB, V, NT, C, JCAP, true>;
+        static_assert(offsetof(SmT, G) % 16 == 0 &&
+                          ((size_t)JCAP * (sizeof(V) + sizeof(int))) % alignof(double) == 0,
+                      "epilogue scratch alignment");
+        unsigned char *rb = reinterpret_cast<unsigned char *>(sm.G);
+        V *bxm = reinterpret_cast<V *>(rb);
+        int *bxe = reinterpret_cast<int *>(rb + (size_t)JCAP * sizeof(V));
+        double *bgq = reinterpret_cast<double *>(rb + (size_t)JCAP * (sizeof(V) + sizeof(int)));
+        static_assert((size_t)JCAP * (sizeof(V) + sizeof(int) + sizeof(double)) <= sizeof(V) * SweepSmem<NB, V, NT, C, JCAP, true>::GSZ,
+                      "epilogue scratch");
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            gq[c] = -INFINITY;
             if (e.bit[c] == -1) {
-                const double lm = sm.lmu[sm.slot[e.idx[c]]];
-                if (lm > -INFINITY) {
-                    gq[c] = (lm - base - (double)xE[c] * kLn2) - (double)xM[c];
-                    if (!isfinite(gq[c])) bad = true;
-                    qmax = fmax(qmax, (V)gq[c]);
+                const int sl = sm.slot[e.idx[c]];
+                if (sl < JCAP) {
+                    bxm[sl] = xM[c];
+                    bxe[sl] = xE[c];
                 }
             }
         }
-        if (bad) atomicOr(a.err, ERR_NONFINITE);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
-        if (lane == 0) sm.fred[w][0] = qmax;
         __syncthreads();
-        if (tid == 0) {
-            V x = V(-INFINITY);
-            for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][0]);
-            const double bx = isfinite((double)x) ? (double)x : 0.0;
-            sm.dred[0] = bx;
-            if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = bx;
-        }
-        __syncthreads();
-        const double bnew = sm.dred[0];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            if (e.bit[c] == -1) {
-                const int i = off + sm.slot[e.idx[c]];
-                a.gj[i] = eps_b * gq[c];
-                const V lp = (V)(gq[c] - bnew);
-                static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
-                sm.lphi[e.idx[c]] = lp;
+        const int ntg = min(sm.ntarget, JCAP);
+        if (a.mode == MODE_UPDATE) {
+            // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base - xE ln 2) - xM   (FP64)
+            V qmax = V(-INFINITY);   // new baseline: the tile maximum of g_j/eps
+            bool bad = false;
+            for (int sl = tid; sl < ntg; sl += NT) {
+                const double lm = sm.lmu[sl];
+                double g = -INFINITY;
+                if (lm > -INFINITY) {
+                    g = (lm - base - (double)bxe[sl] * kLn2) - (double)bxm[sl];
+                    if (!isfinite(g)) bad = true;
+                    qmax = fmax(qmax, (V)g);
+                }
+                bgq[sl] = g;
+                a.gj[off + sl] = eps_b * g;
             }
-        }
-    } else if (a.mode == MODE_RESIDUAL) {
-        double acc = 0.0;
+            if (bad) atomicOr(a.err, ERR_NONFINITE);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            if (e.bit[c] == -1) {
-                const int i = off + sm.slot[e.idx[c]];
+            for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
+            if (lane == 0) sm.fred[w][0] = qmax;
+            __syncthreads();
+            if (tid == 0) {
+                V x = V(-INFINITY);
+                for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][0]);
+                const double bx = isfinite((double)x) ? (double)x : 0.0;
+                sm.dred[0] = bx;
+                if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = bx;
+            }
+            __syncthreads();
+            const double bnew = sm.dred[0];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (e.bit[c] == -1) {
+                    const V lp = (V)(bgq[sm.slot[e.idx[c]]] - bnew);
+                    static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
+                    sm.lphi[e.idx[c]] = lp;
+                }
+            }
+        } else if (a.mode == MODE_RESIDUAL) {
+            double acc = 0.0;
+            for (int sl = tid; sl < ntg; sl += NT) {
+                const int i = off + sl;
                 const double gg = a.gj[i];
-                const double marg = (gg == -INFINITY || xM[c] == V(-INFINITY))
-                                        ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)xE[c] * kLn2 + (double)xM[c]));
+                const double marg = (gg == -INFINITY || bxm[sl] == V(-INFINITY))
+                                        ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)bxe[sl] * kLn2 + (double)bxm[sl]));
                 acc += fabs(marg - a.muj[i]);
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (lane == 0) sm.dred[w] = acc;
-        __syncthreads();
-        if (tid == 0) {
-            double x = 0.0;
-            for (int q = 0; q < NW; ++q) x += sm.dred[q];
-            a.partial[b] = x;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            if (e.bit[c] == -1) {
-                const int i = off + sm.slot[e.idx[c]];
-                const double lnMc = (xM[c] == V(-INFINITY)) ? -INFINITY : base + (double)xE[c] * kLn2 + (double)xM[c];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (lane == 0) sm.dred[w] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                double x = 0.0;
+                for (int q = 0; q < NW; ++q) x += sm.dred[q];
+                a.partial[b] = x;
+            }
+        } else {
+            for (int sl = tid; sl < ntg; sl += NT) {
+                const int i = off + sl;
+                const double lnMc = (bxm[sl] == V(-INFINITY)) ? -INFINITY : base + (double)bxe[sl] * kLn2 + (double)bxm[sl];
                 double r;
                 if (a.mode == MODE_OUT_M)
                     r = exp_acc<V>(lnMc);
@@ -1210,6 +1230,86 @@ __device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const Swee
                 else
                     r = lnMc;
                 a.out[i] = r;
+            }
+        }
+    } else {
+        if (a.mode == MODE_UPDATE) {
+            // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base) - xM   (FP64)
+            double gq[C];
+            V qmax = V(-INFINITY);   // new baseline: the tile maximum of g_j/eps
+            bool bad = false;
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                gq[c] = -INFINITY;
+                if (e.bit[c] == -1) {
+                    const double lm = sm.lmu[sm.slot[e.idx[c]]];
+                    if (lm > -INFINITY) {
+                        gq[c] = (lm - base - (double)xE[c] * kLn2) - (double)xM[c];
+                        if (!isfinite(gq[c])) bad = true;
+                        qmax = fmax(qmax, (V)gq[c]);
+                    }
+                }
+            }
+            if (bad) atomicOr(a.err, ERR_NONFINITE);
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
+            if (lane == 0) sm.fred[w][0] = qmax;
+            __syncthreads();
+            if (tid == 0) {
+                V x = V(-INFINITY);
+                for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][0]);
+                const double bx = isfinite((double)x) ? (double)x : 0.0;
+                sm.dred[0] = bx;
+                if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = bx;
+            }
+            __syncthreads();
+            const double bnew = sm.dred[0];
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (e.bit[c] == -1) {
+                    const int i = off + sm.slot[e.idx[c]];
+                    a.gj[i] = eps_b * gq[c];
+                    const V lp = (V)(gq[c] - bnew);
+                    static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
+                    sm.lphi[e.idx[c]] = lp;
+                }
+            }
+        } else if (a.mode == MODE_RESIDUAL) {
+            double acc = 0.0;
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (e.bit[c] == -1) {
+                    const int i = off + sm.slot[e.idx[c]];
+                    const double gg = a.gj[i];
+                    const double marg = (gg == -INFINITY || xM[c] == V(-INFINITY))
+                                            ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)xE[c] * kLn2 + (double)xM[c]));
+                    acc += fabs(marg - a.muj[i]);
+                }
+            }
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (lane == 0) sm.dred[w] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                double x = 0.0;
+                for (int q = 0; q < NW; ++q) x += sm.dred[q];
+                a.partial[b] = x;
+            }
+        } else {
+    #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (e.bit[c] == -1) {
+                    const int i = off + sm.slot[e.idx[c]];
+                    const double lnMc = (xM[c] == V(-INFINITY)) ? -INFINITY : base + (double)xE[c] * kLn2 + (double)xM[c];
+                    double r;
+                    if (a.mode == MODE_OUT_M)
+                        r = exp_acc<V>(lnMc);
+                    else if (a.mode == MODE_OUT_PLAN)
+                        r = (a.gj[i] == -INFINITY) ? 0.0 : exp_acc<V>(a.gj[i] * inv_eps_b + lnMc);
+                    else
+                        r = lnMc;
+                    a.out[i] = r;
+                }
             }
         }
     }
