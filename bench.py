@@ -135,6 +135,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (the job's time is its slowest
+    replica), followed by a barrier; the value itself for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.barrier()
+    return float(t.item())
+
+
+def job_value(iters_per_step, steps, world, ms_max):
+    """Whole-job throughput: the iterations of all replicas over the slowest
+    replica's time."""
+    return iters_per_step * steps * world / (ms_max / 1000.0)
+
+
 def flush_l2(torch, buf):
     buf.fill_(1.0)
 
@@ -182,12 +200,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = plan.info()["kernel_launches"] - launches0
     clocks = sampler.stop() if sampler else None
-    t_max = ms_total
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        torch.distributed.barrier()
+    t_max = max_over_ranks(ms_total, world, dev)
 
     # per-kernel timing of the same launches with CUDA events on the plan stream
     n_prof = min(20, w["iters"])
@@ -447,8 +460,7 @@ def main():
             torch.distributed.destroy_process_group()
         return 0
 
-    iters_total = w["iters"] * args.steps * world
-    value = iters_total / (r["ms"] / 1000.0)
+    value = job_value(w["iters"], args.steps, world, r["ms"])
     peak, peak_kind = measured_peaks()
     # dominant kernel by total device time in the profiled iterations
     stats = r["stats"]
