@@ -65,8 +65,7 @@ typedef struct {
     int iters;        /* Sinkhorn iterations performed (one = l updates)        */
     double residual;  /* sum over marginals 1..l-1 of ||phi_k . M_k - mu_k||_1
                          after the last iteration (Algorithm 1 / 4, line 7)      */
-    double W;         /* <C, T> of the regularised plan (Eq. k-mmot distance);
-                         NaN for l = 8                                           */
+    double W;         /* <C, T> of the regularised plan (Eq. k-mmot distance)    */
     double primal;    /* <C,T> + eps <T, ln T> = sum_k <g_k, marg_k>             */
     double dual;      /* sum_k <g_k, mu_k> + eps - eps Z                         */
     double mass;      /* Z = sum of all plan entries                             */

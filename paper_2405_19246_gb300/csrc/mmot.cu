@@ -457,7 +457,7 @@ cudaError_t launch_obj(int l, const SweepArgs &a, bool fp64, cudaStream_t st, in
     case 5: return launch_obj_l<5>(a, fp64, st, kind);
     case 6: return launch_obj_l<6>(a, fp64, st, kind);
     case 7: return launch_obj_l<7>(a, fp64, st, kind);
-    default: return cudaErrorInvalidValue;   // l = 8: not built (256 states)
+    default: return cudaErrorInvalidValue;   // l = 8: warp tiles (launch_objective_warp8)
     }
 }
 
@@ -468,7 +468,19 @@ mmot_status ensure_objective_scratch(mmot_plan p)
     const size_t nt = (size_t)p->nt, ns = (size_t)1 << l, sf = p->sfsz;
     CUDA_TRY(p->alloc(&p->o_bc, nt * ns * sf));
     CUDA_TRY(p->alloc(&p->o_lnz, nt));
-    if (l <= kMaxOpBits) {
+    if (l == 8) {
+        // warp tiles: level passes and per-state scans, then the objective kernel
+        CUDA_TRY(p->alloc(&p->o_fc, nt * ns * sf));
+        CUDA_TRY(p->alloc(&p->o_agg, nt * ns * sf));
+        CUDA_TRY(p->alloc(&p->o_decF, p->h_odecF.size()));
+        CUDA_TRY(p->alloc(&p->o_decB, p->h_odecB.size()));
+        CUDA_TRY(p->alloc(&p->o_cflags, (size_t)2 * ns * 32));
+        CUDA_TRY(p->alloc(&p->o_cagg, (size_t)2 * ns * 32 * sf));
+        CUDA_TRY(cudaMemcpyAsync(p->o_decF, p->h_odecF.data(), p->h_odecF.size(), cudaMemcpyHostToDevice, p->st));
+        CUDA_TRY(cudaMemcpyAsync(p->o_decB, p->h_odecB.data(), p->h_odecB.size(), cudaMemcpyHostToDevice, p->st));
+        CUDA_TRY(cudaMemsetAsync(p->o_fc, 0, nt * ns * sf, p->st));
+        CUDA_TRY(cudaMemsetAsync(p->o_bc, 0, nt * ns * sf, p->st));
+    } else if (l <= kMaxOpBits) {
         CUDA_TRY(p->alloc(&p->o_fc, nt * ns * sf));
         CUDA_TRY(p->alloc(&p->o_opF, nt * l * ns * sf));
         CUDA_TRY(p->alloc(&p->o_opB, nt * l * ns * sf));
@@ -509,7 +521,20 @@ mmot_status enqueue_cost(mmot_plan p)
     a.pdecB = p->o_decB;
     a.cflags = p->o_cflags;
     a.cagg = p->o_cagg;
-    if (l <= kMaxOpBits) {
+    if (l == 8) {
+        CUDA_TRY(cudaMemsetAsync(p->o_cflags, 0, sizeof(int) * 2 * 256 * 32, p->st));
+        for (int fwd = 0; fwd < 2; ++fwd) {
+            for (int lv = 1; lv <= l; ++lv) {
+                CUDA_TRY(fp64 ? launch_objective_warp8<double>(a, p->st, 5, lv, fwd)
+                              : launch_objective_warp8<float>(a, p->st, 5, lv, fwd));
+                CUDA_TRY(fp64 ? launch_objective_warp8<double>(a, p->st, 6, lv, fwd)
+                              : launch_objective_warp8<float>(a, p->st, 6, lv, fwd));
+                p->launches += 2;
+            }
+        }
+        CUDA_TRY(fp64 ? launch_objective_warp8<double>(a, p->st, 7, 0, 0)
+                      : launch_objective_warp8<float>(a, p->st, 7, 0, 0));
+    } else if (l <= kMaxOpBits) {
         CUDA_TRY(launch_obj(l, a, fp64, p->st, 2));
         CUDA_TRY(cudaMemsetAsync(p->o_cflags, 0, sizeof(int) * 2 * 32 * (l + 1), p->st));
         CUDA_TRY(launch_obj(l, a, fp64, p->st, 3));
@@ -522,7 +547,7 @@ mmot_status enqueue_cost(mmot_plan p)
     }
     k_sum_partials<<<1, 256, 0, p->st>>>(p->partial, p->nt, p->dsum, 0);
     CUDA_TRY(cudaGetLastError());
-    p->launches += (l <= kMaxOpBits) ? 4 : 3;
+    p->launches += (l == 8) ? 1 : ((l <= kMaxOpBits) ? 4 : 3);
     return MMOT_OK;
 }
 
@@ -878,7 +903,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     // exp(-w_s d) from each tile base to the next base in processing order
     std::vector<unsigned char> hdecF, hdecB;
     const std::vector<int32_t> segv = batch ? hseg : std::vector<int32_t>();
-    if (l <= kMaxOpBits) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB, segv);
+    if (l <= kMaxOpBits || l == 8) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB, segv);
     decay_tables(L, p->NB, fp64, hdecF, hdecB, segv);
     ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
     ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());

@@ -125,8 +125,11 @@ cudaError_t launch_three_phase(int NB, const SweepArgs &a, bool fp64, cudaStream
 // (l <= 4), 5 objective kernel.
 template <int L, typename V>
 cudaError_t launch_objective(const SweepArgs &a, cudaStream_t s, int kind);
-// largest l with objective kernels (l = 8 would need 256 states per point)
-constexpr int kMaxObjectiveL = 7;
+// Objective sweeps of l = 8 marginals on warp tiles (warp.cuh): kind 5 level
+// pass, 6 level scan, 7 objective kernel.
+template <typename V>
+cudaError_t launch_objective_warp8(const SweepArgs &a, cudaStream_t s, int kind, int level, int fwd);
+constexpr int kMaxObjectiveL = 8;
 
 // Tile geometry chosen per (bits, precision): points per tile, threads,
 // maximum points of one marginal in a tile, and the tile span limit

@@ -1469,7 +1469,7 @@ __global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
 // thread composes the maps x -> dec (x + own) of its tiles, the block scans
 // them, the chunk publishes its contribution at the next chunk's base and
 // adds those of the earlier chunks (same instance only; bounded waits).
-template <int NB, typename V>
+template <int NB, typename V, int LM = NB + 1>
 __global__ void __launch_bounds__(256) k_lscan(SweepArgs a, int SL, int fwd_i)
 {
     constexpr int NS = 1 << NB;
@@ -1586,7 +1586,7 @@ __global__ void __launch_bounds__(256) k_lscan(SweepArgs a, int SL, int fwd_i)
         __syncwarp();
         if (lane == 0) st_release(cflag + c, 1);
         // carry into this chunk: contributions of the earlier chunks of the same instance
-        const double ws = (double)(SL * (NB + 1 - SL));
+        const double ws = (double)(SL * (LM - SL));
         const double ub = chunk_base(c);
         Sf<V> part = sf_zero<V>();
         bool fail = false;

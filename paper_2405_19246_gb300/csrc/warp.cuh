@@ -23,11 +23,13 @@
 
 namespace mmot {
 
-template <int NB, typename V>
+// NB state bits; LM marginals in the cost (NB + 1 for a marginal product, NB
+// for the all-subset sweeps of the objective).
+template <int NB, typename V, int LM = NB + 1>
 struct WarpRun {
     static constexpr int NS = 1 << NB;
     static constexpr int NQ = NS / 32;
-    static constexpr int L = NB + 1;
+    static constexpr int L = LM;
     static constexpr unsigned FULL = 0xffffffffu;
     Sf<V> f[NQ];
     V D[NB + 1];         // D[s] = max(0, a_s span), s = 1..NB
@@ -141,6 +143,70 @@ struct WarpRun {
     }
 };
 
+// Objective walk: every point injects (no target); on_point(id, p) is called
+// before (PRE) or after the point's injection with the tile-local index.
+// Only the points at processing positions [r0, r1) of the n-point tile are
+// walked (position = index forward, n - 1 - index backward).
+template <int NB, typename V, int LM, bool PRE, typename OnP>
+__device__ void warp_run_each(WarpRun<NB, V, LM> &r, const SweepArgs &a, uint32_t t0, int n, bool fwd,
+                              int r0, int r1, OnP &&on_point)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NQ = WarpRun<NB, V, LM>::NQ;
+    const V *pos = static_cast<const V *>(a.pos);
+    const V *lphi = static_cast<const V *>(a.lphi);
+    const int lane = r.lane;
+    for (int c0 = r0; c0 < r1; c0 += 32) {
+        const int rr = c0 + lane;
+        V pp = V(0), lp = V(0);
+        int bit = -2, idl = 0;
+        if (rr < r1) {
+            idl = fwd ? rr : n - 1 - rr;
+            bit = a.mid[t0 + idl];
+            const V x = pos[t0 + idl];
+            pp = fwd ? x : r.span - x;
+            lp = lphi[t0 + idl];
+        }
+        const int cnt = min(32, r1 - c0);
+        for (int i = 0; i < cnt; ++i) {
+            const int k = __shfl_sync(FULL, bit, i);
+            const V p = __shfl_sync(FULL, pp, i);
+            const int id = __shfl_sync(FULL, idl, i);
+            if constexpr (PRE) on_point(id, p);
+            const V l = __shfl_sync(FULL, lp, i);
+            V facl = V(0);
+            if (lane < NB) {
+                const int s = lane + 1;
+                facl = vexp<V>(l + (V)(r.rate(s) - r.rate(s - 1)) * p - r.D[s]);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int T = lane + 32 * q;
+                const V fac = __shfl_sync(FULL, facl, (popc_c(T) + 31) & 31);
+                Sf<V> src;
+                if (k < 5) {
+                    src.m = __shfl_xor_sync(FULL, r.f[q].m, 1 << k);
+                    src.k = __shfl_xor_sync(FULL, r.f[q].k, 1 << k);
+                } else {
+                    src = r.f[0];
+#pragma unroll
+                    for (int q2 = 0; q2 < NQ; ++q2)
+                        if (q2 == (q ^ (1 << (k - 5)))) src = r.f[q2];
+                }
+                if ((T >> k) & 1) {
+                    if ((T ^ (1 << k)) == 0) src = Sf<V>{V(0.5), 1};
+                    if (src.m != V(0)) {
+                        Sf<V> t = sf_make<V>(src.m * fac);
+                        t.k += src.k;
+                        if (t.m != V(0)) r.f[q] = sf_add(r.f[q], t);
+                    }
+                }
+            }
+            if constexpr (!PRE) on_point(id, p);
+        }
+    }
+}
+
 // number of target points of the tile
 __device__ __forceinline__ int warp_count_targets(const SweepArgs &a, uint32_t t0, int n, int j)
 {
@@ -163,7 +229,7 @@ __device__ __forceinline__ void warp_betas(const SweepArgs &a, int b, int j, int
 // Level pass: the tile's own contribution to the states of level SL at its
 // base, from the carries of the lower levels.  4 warps per block, one tile
 // per warp.
-template <int NB, typename V>
+template <int NB, typename V, int LM = NB + 1>
 __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
 {
     constexpr int NS = 1 << NB;
@@ -175,16 +241,16 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
     const int n = (int)(a.tstart[b + 1] - t0);
     double beta[NB];
     warp_betas(a, b, a.j, NB, beta);
-    WarpRun<NB, V> r;
+    WarpRun<NB, V, LM> r;
     r.init(a, b);
     r.load_carries(sfp<V>(fwd ? a.fcarry : a.bcarry), b, beta, SL);
     r.run(a, t0, n, a.j, fwd, 0, [](int, V) {});
 #pragma unroll
-    for (int q = 0; q < WarpRun<NB, V>::NQ; ++q) {
+    for (int q = 0; q < WarpRun<NB, V, LM>::NQ; ++q) {
         const int T = r.lane + 32 * q;
         if (popc_c(T) == SL)
             sfp<V>(a.agg)[(size_t)b * NS + T] =
-                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V>::sum_beta(beta, T) + r.gam[SL]));
+                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V, LM>::sum_beta(beta, T) + r.gam[SL]));
     }
 }
 
@@ -333,6 +399,154 @@ cudaError_t launch_wpass_impl(const SweepArgs &a, cudaStream_t st, int SL, int f
 {
     k_wpass<NB, V><<<(a.nt + 3) / 4, 128, 0, st>>>(a, SL, fwd);
     return cudaGetLastError();
+}
+
+// Objective of l = NB marginals on warp tiles (all 2^l subsets, no target):
+// W = <C, T> by the gap formula, as in objective.cuh.  The tile is taken in
+// chunks of CH points: a backward walk from the tile's end keeps the
+// backward states including each point of the chunk in shared memory, then
+// the forward walk over the chunk adds, before each point's injection,
+// (x_t - x_{t-1}) sum_S w_|S| F_S G_{S^c} with F_S G_{S^c} formed as
+// mantissa x 2^exponent.  Per tile: partial[b] = eps W_b / Z_b, out[b] = ln Z.
+template <int NB, typename V, int CH>
+__global__ void __launch_bounds__(32) k_wobj(SweepArgs a)
+{
+    using R = WarpRun<NB, V, NB>;
+    constexpr int NS = 1 << NB;
+    constexpr int NQ = R::NQ;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char wsm[];
+    SfT<V> *Gall = reinterpret_cast<SfT<V> *>(wsm);
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t t0 = a.tstart[b];
+    const int n = (int)(a.tstart[b + 1] - t0);
+    double beta[NB];
+    warp_betas(a, b, a.j, NB, beta);
+    double sb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) sb += beta[k];
+
+    R rb;
+    rb.init(a, b);
+    R rf;
+    rf.init(a, b);
+    rf.load_carries(sfp<V>(a.fcarry), b, beta, NB + 1);
+    // exp(gamma^F_s + gamma^G_{l-s} - w_s span) = mu_s 2^(n_s), by lane s
+    int en = 0;
+    V em = V(0);
+    if (lane <= NB) {
+        const int s = lane;
+        const double c = (rf.gam[s] + rb.gam[NB - s] - (double)R::rate(s) * (double)rf.span) * kLog2e;
+        const double fl = floor(c);
+        en = (int)fl;
+        em = vexp2<V>((V)(c - fl));
+    }
+    const bool first = (b == 0) || (a.seg && a.seg[b - 1] != a.seg[b]);
+    const V gap0 = first ? V(0) : (V)(a.ulb[b] - a.urb[b - 1]);
+    const V *pos = static_cast<const V *>(a.pos);
+    Sf<V> accW = sf_zero<V>(), accZ = sf_zero<V>();
+    for (int c0 = 0; c0 < n; c0 += CH) {
+    const int c1 = min(n, c0 + CH);
+    // backward states including each point of [c0, c1)
+    rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
+    __syncwarp();
+    warp_run_each<NB, V, NB, false>(rb, a, t0, n, false, 0, n - c0, [&](int id, V) {
+        if (id < c1) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) Gall[(size_t)(id - c0) * NS + lane + 32 * q] = sf_store(rb.f[q]);
+        }
+    });
+    __syncwarp();
+    warp_run_each<NB, V, NB, true>(rf, a, t0, n, true, c0, c1, [&](int id, V) {
+        int Emax = INT_MIN / 2;
+        V sw = V(0), sz = V(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int S = lane + 32 * q;
+            const int s = popc_c(S);
+            const int ens = __shfl_sync(FULL, en, s);
+            const V ems = __shfl_sync(FULL, em, s);
+            const Sf<V> fS = (S == 0) ? Sf<V>{V(0.5), 1} : rf.f[q];
+            const int U = (NS - 1) ^ S;
+            const Sf<V> gU = (U == 0) ? Sf<V>{V(0.5), 1} : sf_load<V>(Gall[(size_t)(id - c0) * NS + U]);
+            if (fS.m != V(0) && gU.m != V(0)) {
+                const Sf<V> z = sf_make<V>(fS.m * gU.m * ems);
+                const int E = z.k + fS.k + gU.k + ens;
+                const V wz = (V)R::rate(s) * z.m;
+                if (E > Emax) {
+                    const V r = pow2neg<V>(Emax - E);
+                    sw = fma(sw, r, wz);
+                    sz = fma(sz, r, z.m);
+                    Emax = E;
+                } else {
+                    const V r = pow2neg<V>(E - Emax);
+                    sw = fma(wz, r, sw);
+                    sz = fma(z.m, r, sz);
+                }
+            }
+        }
+        int Ew = Emax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Ew = max(Ew, __shfl_xor_sync(FULL, Ew, o));
+        const V r = (sz > V(0)) ? pow2neg<V>(Emax - Ew) : V(0);
+        V tw = sw * r, tz = sz * r;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tw += __shfl_xor_sync(FULL, tw, o);
+            tz += __shfl_xor_sync(FULL, tz, o);
+        }
+        if (tz > V(0)) {
+            const V dx = (id > 0) ? pos[t0 + id] - pos[t0 + id - 1] : gap0;
+            Sf<V> t = sf_make<V>(dx * tw);
+            t.k += Ew;
+            if (t.m != V(0)) accW = sf_add(accW, t);
+            if (id == 0) {
+                accZ = sf_make<V>(tz);
+                accZ.k += Ew;
+            }
+        }
+    });
+    }
+    if (lane == 0) {
+        if (accZ.m == V(0)) {
+            a.partial[b] = 0.0;
+            a.out[b] = -INFINITY;
+        } else {
+            const double rr = (accW.m == V(0)) ? 0.0 : ldexp((double)accW.m / (double)accZ.m, accW.k - accZ.k);
+            a.partial[b] = tile_eps(a, b) * rr;
+            a.out[b] = log((double)accZ.m) + (double)accZ.k * kLn2 + sb;
+        }
+    }
+}
+
+// objective launches for l = NB marginals on warp tiles of K points:
+// kind 5 level pass, 6 level scan, 7 objective kernel
+template <int NB, typename V, int K>
+cudaError_t launch_wobj_impl(const SweepArgs &a, cudaStream_t st, int kind, int SL, int fwd)
+{
+    if (kind == 5) {
+        k_wpass<NB, V, NB><<<(a.nt + 3) / 4, 128, 0, st>>>(a, SL, fwd);
+        return cudaGetLastError();
+    }
+    if (kind == 6) {
+        int nst = 0;
+        for (int S = 1; S < (1 << NB); ++S)
+            if (popc_c(S) == SL) ++nst;
+        const dim3 grid(lscan_chunks(a.nt, nst), nst);
+        k_lscan<NB, V, NB><<<grid, 256, 0, st>>>(a, SL, fwd);
+        return cudaGetLastError();
+    }
+    if (kind == 7) {
+        constexpr int CH = 16;   // points whose backward states are kept at once
+        const size_t sz = (size_t)CH * (1 << NB) * sizeof(SfT<V>);
+        auto kern = k_wobj<NB, V, CH>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
+        if (e != cudaSuccess) return e;
+        kern<<<a.nt, 32, sz, st>>>(a);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int NB, typename V>
