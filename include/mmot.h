@@ -18,8 +18,8 @@
  *
  * Potentials.  The library stores g_k = eps ln phi_k (FP64).  The paper's dual
  * variables are alpha_k = -g_k - eps/l (Sec. 2, definition of phi).  A zero
- * weight gives g = -inf.  Initial potentials are phi = 1/N_k (Algorithm 1,
- * line 1), i.e. g_k = -eps ln N_k.
+ * weight gives g = -inf.  Initial potentials are phi = 1/N_k (the
+ * initialisation of Algorithm 1), i.e. g_k = -eps ln N_k.
  *
  * Conventions for every call:
  *   - Calls never throw and never abort; they return an mmot_status.  On an
@@ -64,7 +64,7 @@ typedef enum {
 typedef struct {
     int iters;        /* Sinkhorn iterations performed (one = l updates)        */
     double residual;  /* sum over marginals 1..l-1 of ||phi_k . M_k - mu_k||_1
-                         after the last iteration (Algorithm 1 / 4, line 7)      */
+                         after the last iteration (stopping test of Algorithm 1 / 4) */
     double W;         /* <C, T> of the regularised plan (Eq. k-mmot distance)    */
     double primal;    /* <C,T> + eps <T, ln T> = sum_k <g_k, marg_k>             */
     double dual;      /* sum_k <g_k, mu_k> + eps - eps Z                         */
@@ -99,7 +99,7 @@ mmot_status mmot_marginal(mmot_plan p, int k, int plan_marginal, double *out);
 
 /* Run n_iters Gauss-Seidel Sinkhorn iterations (Sec. 4.2 update formulas;
  * Algorithm 4 loop body): for j = 1..l, g_j <- eps (ln mu_j - ln M_j).
- * If residual_out is not NULL it receives the residual of Algorithm 1 line 7
+ * If residual_out is not NULL it receives the residual of Algorithm 1's stopping test
  * (sum over marginals 1..l-1 of ||phi_k . M_k - mu_k||_1) after the last
  * iteration, which costs l-1 extra marginal products. */
 mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out);
@@ -120,8 +120,9 @@ mmot_status mmot_objective(mmot_plan p, mmot_result *out);
 mmot_status mmot_get_potentials(mmot_plan p, int k, double *g_out);
 mmot_status mmot_set_potentials(mmot_plan p, int k, const double *g_in);
 
-/* Reset every potential to the starting point phi_k = 1/N_k (Algorithm 1,
- * line 1), i.e. g_k = -eps ln N_k, on the device (no host transfer). */
+/* Reset every potential to the starting point phi_k = 1/N_k (the
+ * initialisation of Algorithm 1), i.e. g_k = -eps ln N_k, on the device (no
+ * host transfer). */
 mmot_status mmot_reset_potentials(mmot_plan p);
 
 /* Plan options (integers):
