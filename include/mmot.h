@@ -77,7 +77,7 @@ typedef struct {
  *   x      l pointers (host or device, see inputs_on_device) to N[k] FP64
  *          support points each, nondecreasing (else MMOT_ERR_UNSORTED).
  *   mu     l pointers to N[k] FP64 weights, >= 0, each summing to 1 within
- *          1e-9 (else MMOT_ERR_INVALID_ARG).  Zero weights are allowed.
+ *          1e-12 (else MMOT_ERR_INVALID_ARG).  Zero weights are allowed.
  *   eps    entropic regularisation, > 0 and finite.
  *   prec   MMOT_FP64 or MMOT_FP32_SCAN_FP64_POT.
  *   inputs_on_device  0: x and mu are host pointers; 1: device pointers.
@@ -131,8 +131,14 @@ mmot_status mmot_reset_potentials(mmot_plan p);
  *   MMOT_OPT_USE_GRAPH     capture the per-iteration launches in a CUDA graph (default 1)
  *   MMOT_OPT_PROFILE       1: bracket every kernel launch with CUDA events on the
  *                          plan's stream and accumulate per-kernel times (graphs
- *                          are not used while profiling); 0: off (default) */
-enum { MMOT_OPT_CHECK_EVERY = 1, MMOT_OPT_SPIN_LIMIT = 2, MMOT_OPT_USE_GRAPH = 3, MMOT_OPT_PROFILE = 4 };
+ *                          are not used while profiling); 0: off (default)
+ *   MMOT_OPT_TEST_HOLD     test hook for the timeout path, 0 (default) or 1: the
+ *                          first chunk of each carry scan never publishes its
+ *                          flags, so the bounded waits of the later chunks run
+ *                          out and calls return MMOT_ERR_TIMEOUT (results are
+ *                          then undefined).  Needs more tiles than one chunk. */
+enum { MMOT_OPT_CHECK_EVERY = 1, MMOT_OPT_SPIN_LIMIT = 2, MMOT_OPT_USE_GRAPH = 3, MMOT_OPT_PROFILE = 4,
+       MMOT_OPT_TEST_HOLD = 5 };
 mmot_status mmot_set_option(mmot_plan p, int option, int64_t value);
 
 /* Per-kernel launch statistics collected while MMOT_OPT_PROFILE is on.
@@ -157,8 +163,18 @@ typedef struct {
     int launches_per_iteration;
     int precision;
     int64_t kernel_launches;   /* library kernels launched on this plan so far */
+    int64_t device_bytes;      /* device memory held by the plan */
 } mmot_plan_info;
 mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
+
+/* Process-wide cap on the device memory that all plans (and the plans inside
+ * batches) may hold together, in bytes; 0 (the default) means no cap.  It
+ * lets a caller that shares the GPU with other work, such as a serving loop
+ * admitting requests by a memory budget, bound the library's footprint: a
+ * creation that would exceed the cap fails with MMOT_ERR_OOM before the
+ * allocation that would cross it, and frees what it had taken.  Memory held
+ * by existing plans is not affected.  bytes < 0: MMOT_ERR_INVALID_ARG. */
+mmot_status mmot_set_memory_limit(int64_t bytes);
 
 /* One marginal product without any device memory allocation.
  *
@@ -176,15 +192,18 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
  *                 device; device when plan_marginal = 1);
  *   k, plan_marginal  as in mmot_marginal (0: M_k, 1: phi_k M_k, 2: ln M_k);
  *   out           N[k] FP64 values, device memory (caller-owned);
- *   cuda_stream   stream to use (borrowed); the call synchronises it before
- *                 returning.
+ *   cuda_stream   stream to use (borrowed).  The inputs are read in the
+ *                 order of that stream (after work the caller queued on it),
+ *                 and the call is synchronous: it synchronises the stream
+ *                 before returning.  Do not issue it on a stream that is
+ *                 being captured into a CUDA graph.
  * Limits: 2 <= l <= 5, sum N <= 2^19 points, at most 1024 tiles; larger
  * problems return MMOT_ERR_RANGE with a message.  Working storage is one
  * static 8 MiB device array per GPU, held by every GPU that loads the library
  * until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (for example from several host threads) race. */
+ * device address (cudaGetSymbolAddress).  All calls share the array: calls
+ * that overlap on the same GPU (from several host threads or streams) race,
+ * so callers must serialise them. */
 mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const double *const *x,
                                   const double *const *g, double eps, int k, int plan_marginal,
                                   double *out, void *cuda_stream);

@@ -572,12 +572,14 @@ int mo_fs3(int64_t N, const double *u, const double *v, const double *w, double 
 /* General-l Sinkhorn in the log domain.                                */
 /* ------------------------------------------------------------------ */
 
-/* Sum_k ||phi_k . M_k - mu_k||_1 over all l marginals, from ln M_k. */
-static double residual_from(int l, const int64_t *N, const double *const *mu,
+/* Sum over marginals k < kend of ||phi_k . M_k - mu_k||_1, from ln M_k.  The
+ * stopping test of Algorithm 1 sums marginals 1..l-1 (kend = l - 1): the last
+ * marginal is exact right after its update. */
+static double residual_from(int kend, const int64_t *N, const double *const *mu,
                             double *const *g, double eps, double *const *lnM)
 {
     double res = 0.0;
-    for (int k = 0; k < l; ++k)
+    for (int k = 0; k < kend; ++k)
         for (int64_t i = 0; i < N[k]; ++i) {
             double a = g[k][i] / eps + lnM[k][i];
             double marg = (a == -INFINITY) ? 0.0 : exp(a);
@@ -597,7 +599,8 @@ static void update_potential(int64_t n, const double *mu, const double *lnM, dou
 /* Gauss-Seidel Sinkhorn.  g[k] must hold the starting potentials (the paper
  * starts from phi = 1/N, i.e. g = -eps ln N_k) and receives the final ones.
  * Each iteration updates j = 1..l in order; then Res is the summed L1 marginal
- * error of all l marginals at the end of the iteration; the loop runs while
+ * error of marginals 1..l-1 at the end of the iteration (the stopping test of
+ * Algorithm 1; marginal l is exact after its update); the loop runs while
  * t < itr_max and Res > tol (Algorithm 1 loop).  With tol <= 0 the residual is
  * evaluated only once, after the last iteration (the loop cannot stop early).
  * Outputs: iterations, residual, W = <C,T>, primal sum_k <g_k, marg_k>,
@@ -625,14 +628,14 @@ int mo_sinkhorn(int l, const int64_t *N, const double *const *x, const double *c
             double lnZ, Wv;
             rc = mo_allpass(l, N, x, (const double *const *)g, eps, lnM, &lnZ, &Wv);
             if (rc) goto done;
-            Res = residual_from(l, N, mu, g, eps, lnM);
+            Res = residual_from(l - 1, N, mu, g, eps, lnM);
         }
     }
     {
         double lnZ, Wv;
         rc = mo_allpass(l, N, x, (const double *const *)g, eps, lnM, &lnZ, &Wv);
         if (rc) goto done;
-        if (t == 0) Res = residual_from(l, N, mu, g, eps, lnM);
+        if (t == 0) Res = residual_from(l - 1, N, mu, g, eps, lnM);
         double P = 0.0, D = 0.0;
         for (int k = 0; k < l; ++k)
             for (int64_t i = 0; i < N[k]; ++i) {

@@ -24,12 +24,13 @@ MMOT_OPT_CHECK_EVERY = 1
 MMOT_OPT_SPIN_LIMIT = 2
 MMOT_OPT_USE_GRAPH = 3
 MMOT_OPT_PROFILE = 4
+MMOT_OPT_TEST_HOLD = 5
 
 # every symbol include/mmot.h declares
 EXPORTED = [
     "mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve", "mmot_objective",
     "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
-    "mmot_get_profile", "mmot_get_info", "mmot_marginal_noalloc",
+    "mmot_get_profile", "mmot_get_info", "mmot_set_memory_limit", "mmot_marginal_noalloc",
     "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_freeze", "mmot_batch_status",
     "mmot_batch_get_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
     "mmot_destroy", "mmot_last_error",
@@ -45,7 +46,7 @@ class MmotPlanInfo(ctypes.Structure):
     _fields_ = [("total_points", ctypes.c_int64), ("tiles", ctypes.c_int64),
                 ("tile_points", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("launches_per_iteration", ctypes.c_int), ("precision", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 
 class MmotBatchInfo(ctypes.Structure):
@@ -84,6 +85,7 @@ def lib():
         L.mmot_set_option.argtypes = [vp, i, i64]
         L.mmot_get_profile.argtypes = [vp, i, P(i64), P(d), i]
         L.mmot_get_info.argtypes = [vp, P(MmotPlanInfo)]
+        L.mmot_set_memory_limit.argtypes = [i64]
         L.mmot_marginal_noalloc.argtypes = [i, P(i64), P(vp), P(vp), d, i, i, vp, vp]
         L.mmot_batch_create.argtypes = [i, P(i), P(i64), P(vp), P(vp), P(d), i, i, vp, P(vp)]
         L.mmot_batch_step.argtypes = [vp, i, d, P(i)]

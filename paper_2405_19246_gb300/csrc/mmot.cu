@@ -35,6 +35,11 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// process-wide cap on the device bytes held by plans (0: none) and the bytes
+// they hold now
+std::atomic<int64_t> g_mem_limit{0};
+std::atomic<int64_t> g_mem_used{0};
+
 }  // namespace
 
 namespace mmot {
@@ -131,6 +136,8 @@ struct mmot_plan_s {
     int check_every = 10;
     int spin_limit = 1 << 23;
     int use_graph = 1;
+    int hold = 0;           // test hook (MMOT_OPT_TEST_HOLD)
+    int64_t dev_bytes = 0;  // device memory held by this plan
     // host copies needed to re-centre potentials
     std::vector<uint8_t> h_mid;
     std::vector<uint32_t> h_tile_of;   // tile of each merged point
@@ -209,6 +216,7 @@ struct mmot_plan_s {
         }
         if (graph) cudaGraphExecDestroy(graph);
         for (void *p : allocs) cudaFree(p);
+        g_mem_used -= dev_bytes;
         if (own_stream && st) cudaStreamDestroy(st);
     }
 
@@ -216,10 +224,15 @@ struct mmot_plan_s {
     cudaError_t alloc(Tp **p, size_t n)
     {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(1, n) * sizeof(Tp));
+        const int64_t bytes = (int64_t)(std::max<size_t>(1, n) * sizeof(Tp));
+        const int64_t lim = g_mem_limit.load();
+        if (lim > 0 && g_mem_used.load() + bytes > lim) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaMalloc(&q, (size_t)bytes);
         if (e == cudaSuccess) {
             allocs.push_back(q);
             *p = static_cast<Tp *>(q);
+            dev_bytes += bytes;
+            g_mem_used += bytes;
         }
         return e;
     }
@@ -333,6 +346,7 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.nt = p->nt;
     a.mode = mode;
     a.spin_limit = p->spin_limit;
+    a.hold = p->hold;
     a.eps = p->eps;
     a.inv_eps = 1.0 / p->eps;
     a.tstart = p->tstart;
@@ -751,7 +765,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
                                 (long long)i);
                 sum += m;
             }
-            if (std::fabs((double)sum - 1.0) > 1e-9)
+            if (std::fabs((double)sum - 1.0) > 1e-12)
                 return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, (double)sum);
             hmu[k].insert(hmu[k].end(), qmu[k].begin(), qmu[k].end());
             seg_off[(size_t)(q + 1) * l + k] = seg_off[(size_t)q * l + k] + n;
@@ -1185,6 +1199,13 @@ mmot_status mmot_set_option(mmot_plan p, int option, int64_t value)
     case MMOT_OPT_PROFILE:
         p->profile = value ? 1 : 0;
         return MMOT_OK;
+    case MMOT_OPT_TEST_HOLD:
+        p->hold = value ? 1 : 0;
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+        return MMOT_OK;
     default: return fail(MMOT_ERR_INVALID_ARG, "unknown option %d", option);
     }
 }
@@ -1245,6 +1266,14 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
     info->launches_per_iteration = p->l * launches_per_product(p);
     info->precision = p->prec;
     info->kernel_launches = p->launches;
+    info->device_bytes = p->dev_bytes;
+    return MMOT_OK;
+}
+
+mmot_status mmot_set_memory_limit(int64_t bytes)
+{
+    if (bytes < 0) return fail(MMOT_ERR_INVALID_ARG, "memory limit < 0");
+    g_mem_limit = bytes;
     return MMOT_OK;
 }
 

@@ -44,6 +44,7 @@ struct SweepArgs {
     int nt;          // tiles
     int mode;
     int spin_limit;  // polls before a wait gives up
+    int hold;        // test hook: the first chunk of a carry scan never publishes its flags
     double eps;
     double inv_eps;
     // per tile

@@ -124,12 +124,17 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     // ---- inputs to the host (cudaMemcpyDefault: host or device pointers) ----
+    // The reads are issued on the caller's stream, so they are ordered after
+    // whatever the caller queued there (for example the kernel that wrote g).
     std::vector<std::vector<double>> hx(l), hg(l);
     for (int q = 0; q < l; ++q) {
         hx[q].resize(N[q]);
         hg[q].resize(N[q]);
-        NA_TRY(cudaMemcpy(hx[q].data(), x[q], sizeof(double) * N[q], cudaMemcpyDefault));
-        NA_TRY(cudaMemcpy(hg[q].data(), g[q], sizeof(double) * N[q], cudaMemcpyDefault));
+        NA_TRY(cudaMemcpyAsync(hx[q].data(), x[q], sizeof(double) * N[q], cudaMemcpyDefault, st));
+        NA_TRY(cudaMemcpyAsync(hg[q].data(), g[q], sizeof(double) * N[q], cudaMemcpyDefault, st));
+    }
+    NA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < l; ++q) {
         for (int64_t i = 0; i < N[q]; ++i) {
             if (!std::isfinite(hx[q][i])) return err_msg(MMOT_ERR_INVALID_ARG, "x[%d][%lld] not finite", q, (long long)i);
             if (i > 0 && hx[q][i] < hx[q][i - 1])
@@ -260,6 +265,7 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     int herr = 0;
     NA_TRY(cudaMemcpyAsync(&herr, scratch + o_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));
+    if (herr & ERR_TIMEOUT) return err_msg(MMOT_ERR_TIMEOUT, "an inter-tile wait reached its poll limit");
     if (herr & ERR_RANGE) return err_msg(MMOT_ERR_RANGE, "a tile exceeded its target-point capacity");
     if (herr & ERR_NONFINITE) return err_msg(MMOT_ERR_NONFINITE, "a product became NaN or infinite");
     if (herr) return err_msg(MMOT_ERR_CUDA, "kernel error flags %d", herr);

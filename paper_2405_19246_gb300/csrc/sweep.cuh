@@ -1584,7 +1584,7 @@ __global__ void __launch_bounds__(256) k_lscan(SweepArgs a, int SL, int fwd_i)
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release(cflag + c, 1);
+        if (lane == 0 && !(a.hold && c == 0)) st_release(cflag + c, 1);
         // carry into this chunk: contributions of the earlier chunks of the same instance
         const double ws = (double)(SL * (LM - SL));
         const double ub = chunk_base(c);
@@ -1795,7 +1795,7 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
             }
             __threadfence();
             __syncwarp();
-            if (lane == 0) st_release(myflag, 1);
+            if (lane == 0 && !(a.hold && c == 0)) st_release(myflag, 1);
             // carry into this chunk: contributions of all earlier chunks
             const double ws = (double)(s * (L - s));
             const double ub = chunk_base(c);

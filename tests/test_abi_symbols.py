@@ -66,3 +66,12 @@ def test_batch_rejects_bad_arguments_without_gpu():
     assert b"instance 1: l = 9" in L.mmot_last_error()
     assert L.mmot_batch_create(2, ls, N, X, X, eps, 1, -1, None, ctypes.byref(h)) == 1
     L.mmot_batch_destroy(None)
+
+
+def test_memory_limit_arguments_without_gpu():
+    from paper_2405_19246_gb300 import _build, _native
+    _build.build()
+    L = _native.lib()
+    assert L.mmot_set_memory_limit(-1) == 1
+    assert b"memory limit" in L.mmot_last_error()
+    assert L.mmot_set_memory_limit(0) == 0
