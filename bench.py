@@ -50,13 +50,13 @@ WORKLOADS = {
 # it was measured on (null when the source has changed since).
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum, one k_prod launch (cold cache)
-    ("large", "fp32", "k_prod", "e52a6f6ccbd2a00a"): 46806784 + 132864,
+
 }
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "shapes.cuh", "mmot_internal.cuh"):
+    for f in ("sweep.cuh", "tile.cuh", "shapes.cuh", "mmot_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2405_19246_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -466,10 +466,12 @@ def main():
     stats = r["stats"]
     T = w["l"] * w["N"]
     esz = 4 if args.precision == "fp32" else 8
-    stream = T * (2 * esz + 1)           # position, ln phi (esz B each) and marginal id
-    target_io = w["N"] * (16 + esz)      # ln mu read, g write, ln phi write at the N_j targets
-    kbytes = {"k_fwd": stream + target_io, "k_prod": stream + target_io, "k_bwd": stream,
-              "k_tileop": stream, "k_carry": None, "k_wprod": stream + target_io,
+    stream = T * (2 * esz + 1)           # position, scaled phi (esz B each) and marginal id
+    # at the N_j targets: ln mu read (double-FP32 or FP64, 8 B), g write (8 B),
+    # scaled phi and ln phi writes (esz B each)
+    target_io = w["N"] * (16 + 2 * esz)
+    kbytes = {"k_fwd": stream + target_io, "k_tile": stream + target_io, "k_bwd": stream,
+              "k_tops": stream, "k_carry": None, "k_wprod": stream + w["N"] * (16 + esz),
               "k_wpass": stream, "k_lscan": None}
     dom = max(stats, key=lambda k: stats[k][1])
     n_dom, ms_dom = stats[dom]

@@ -141,8 +141,8 @@ class Plan:
     def profile_stats(self, reset=True):
         """{kernel name: (launches, total ms)} from the CUDA-event profile."""
         out = {}
-        names = ((0, "k_bwd"), (1, "k_fwd"), (2, "k_tileop"), (3, "k_carry"),
-                 (4, "k_prod" if self.l <= 5 else "k_wprod"), (5, "k_wpass"), (6, "k_lscan"))
+        names = ((0, "k_bwd"), (1, "k_fwd"), (2, "k_tops"), (3, "k_carry"),
+                 (4, "k_tile" if self.l <= 5 else "k_wprod"), (5, "k_wpass"), (6, "k_lscan"))
         for k, name in names:
             n = ctypes.c_int64()
             ms = ctypes.c_double()

@@ -143,6 +143,7 @@ struct mmot_plan_s {
     std::vector<uint32_t> h_tile_of;   // tile of each merged point
     std::vector<uint32_t> h_mpos[MMOT_MAXL];  // merged index of each local point
     std::vector<uint32_t> h_tstart;
+    std::vector<uint32_t> h_toff;   // padded stream offset of each tile (l <= 5)
     std::vector<int32_t> h_reftile;
     std::vector<double> h_beta;
     std::vector<double> h_beta0;   // baselines of the initial potentials
@@ -172,6 +173,12 @@ struct mmot_plan_s {
     double *beta = nullptr;
     double *g[MMOT_MAXL] = {nullptr};
     double *lnmu[MMOT_MAXL] = {nullptr};
+    float2 *lnmu_ff[MMOT_MAXL] = {nullptr};   // ln mu as FP32 hi + lo (FP32 path, l <= 5)
+    // padded stream of the tile kernels (l <= 5): e^{pos}, scaled phi, marginal
+    int64_t Tpad = 0;
+    uint32_t *toff = nullptr;
+    void *epos = nullptr, *ephi = nullptr;
+    uint8_t *emid = nullptr;
     double *mu[MMOT_MAXL] = {nullptr};
     // scaled floats: float2 (FP32 path) or double2 (FP64 path), sfsz bytes each
     unsigned char *agg = nullptr, *inc = nullptr, *bcarry = nullptr;
@@ -371,6 +378,11 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.pdecB = p->pdecB;
     a.cflags = p->cflags;
     a.cagg = p->cagg;
+    a.toff = p->toff;
+    a.epos = p->epos;
+    a.ephi = p->ephi;
+    a.emid = p->emid;
+    a.lnmuj_ff = (j < p->l) ? p->lnmu_ff[j] : nullptr;
     a.jnext = -1;
     // j = l: no target marginal (objective sweeps)
     a.gj = (j < p->l) ? p->g[j] : nullptr;
@@ -572,6 +584,14 @@ __global__ void k_reset(double *g, int64_t n, double v)
         g[i] = v;
 }
 
+// x[i] = v for i < n (the scaled phi of the tile kernels after a reset)
+template <typename Tv>
+__global__ void k_fill(Tv *x, int64_t n, Tv v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
 // g_k of instance q (one block per instance) = its initial value
 __global__ void k_reset_seg(double *g, const int64_t *off, const double *g0, int k, int l)
 {
@@ -681,6 +701,23 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
         else
             reinterpret_cast<float *>(lp.data())[t] = (float)v;
     }
+    // the same points in the padded stream of the tile kernels: e^{g/eps - beta}
+    std::vector<unsigned char> ep;
+    if (p->three_phase) {
+        ep.resize((size_t)p->Tpad * p->esz);
+        CUDA_TRY(cudaMemcpyAsync(ep.data(), p->ephi, ep.size(), cudaMemcpyDeviceToHost, p->st));
+        CUDA_TRY(cudaStreamSynchronize(p->st));
+        for (int64_t i = 0; i < p->N[k]; ++i) {
+            const uint32_t t = p->h_mpos[k][i];
+            const uint32_t b = p->h_tile_of[t];
+            const size_t u = (size_t)p->h_toff[b] + (t - p->h_tstart[b]);
+            const double v = std::exp(g[i] / p->eps - p->h_beta[(size_t)b * l + k]);
+            if (p->esz == 8)
+                reinterpret_cast<double *>(ep.data())[u] = v;
+            else
+                reinterpret_cast<float *>(ep.data())[u] = (float)v;
+        }
+    }
     // the device beta of other marginals may have moved: read them back first
     std::vector<double> hb((size_t)nt * l);
     CUDA_TRY(cudaMemcpyAsync(hb.data(), p->beta, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, p->st));
@@ -688,6 +725,7 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
     for (int b = 0; b < nt; ++b) hb[(size_t)b * l + k] = p->h_beta[(size_t)b * l + k];
     CUDA_TRY(cudaMemcpyAsync(p->beta, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaMemcpyAsync(p->lphi, lp.data(), lp.size(), cudaMemcpyHostToDevice, p->st));
+    if (p->three_phase) CUDA_TRY(cudaMemcpyAsync(p->ephi, ep.data(), ep.size(), cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaMemcpyAsync(p->g[k], g.data(), sizeof(double) * p->N[k], cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaStreamSynchronize(p->st));
     p->ops_target = -1;
@@ -878,6 +916,27 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     if (p->three_phase) {
         PA(p->opF, (size_t)nt * p->NB * p->NS * p->sfsz);
         PA(p->opB, (size_t)nt * p->NB * p->NS * p->sfsz);
+        // padded stream: every tile starts on a 16-element boundary
+        p->h_toff.resize(nt);
+        int64_t o = 0;
+        for (int b = 0; b < nt; ++b) {
+            p->h_toff[b] = (uint32_t)o;
+            o += ((int64_t)(ts[b + 1] - ts[b]) + 15) / 16 * 16;
+        }
+        p->Tpad = std::max<int64_t>(o, 16);
+        if (p->Tpad >= ((int64_t)1 << 32)) {
+            delete p;
+            return fail(MMOT_ERR_RANGE, "padded stream too long");
+        }
+        PA(p->toff, nt);
+        unsigned char *q1 = nullptr, *q2 = nullptr;
+        PA(q1, (size_t)p->Tpad * p->esz);
+        PA(q2, (size_t)p->Tpad * p->esz);
+        p->epos = q1;
+        p->ephi = q2;
+        PA(p->emid, p->Tpad);
+        if (!fp64)
+            for (int k = 0; k < l; ++k) PA(p->lnmu_ff[k], N[k]);
     }
     PA(p->partial, nt);
     p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);
@@ -948,6 +1007,54 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         ce = ce ? ce : up(p->d_goff, seg_off.data(), sizeof(int64_t) * seg_off.size());
         ce = ce ? ce : up(p->d_g0, g0.data(), sizeof(double) * g0.size());
         ce = ce ? ce : cudaMemsetAsync(p->d_frozen, 0, sizeof(int32_t) * nin, p->st);
+    }
+    if (p->three_phase) {
+        // padded stream: e^{pos}, scaled phi (1: lphi = 0), marginal (0xff: padding)
+        const size_t Tp = (size_t)p->Tpad;
+        std::vector<unsigned char> hep(Tp * p->esz), hph(Tp * p->esz);
+        std::vector<uint8_t> hem(Tp, 0xff);
+        for (size_t u = 0; u < Tp; ++u) {
+            if (fp64) {
+                reinterpret_cast<double *>(hep.data())[u] = 1.0;
+                reinterpret_cast<double *>(hph.data())[u] = 0.0;
+            } else {
+                reinterpret_cast<float *>(hep.data())[u] = 1.0f;
+                reinterpret_cast<float *>(hph.data())[u] = 0.0f;
+            }
+        }
+        for (int b = 0; b < nt; ++b) {
+            for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
+                const size_t u = (size_t)p->h_toff[b] + (t - ts[b]);
+                const double e = std::exp(hpos[t]);
+                if (fp64) {
+                    reinterpret_cast<double *>(hep.data())[u] = e;
+                    reinterpret_cast<double *>(hph.data())[u] = 1.0;
+                } else {
+                    reinterpret_cast<float *>(hep.data())[u] = (float)e;
+                    reinterpret_cast<float *>(hph.data())[u] = 1.0f;
+                }
+                hem[u] = p->h_mid[t];
+            }
+        }
+        ce = ce ? ce : up(p->toff, p->h_toff.data(), sizeof(uint32_t) * nt);
+        ce = ce ? ce : up(p->epos, hep.data(), hep.size());
+        ce = ce ? ce : up(p->ephi, hph.data(), hph.size());
+        ce = ce ? ce : up(p->emid, hem.data(), hem.size());
+        if (!fp64) {
+            for (int k = 0; k < l && ce == cudaSuccess; ++k) {
+                std::vector<float2> ff(N[k]);
+                for (int64_t i = 0; i < N[k]; ++i) {
+                    const double v = hlm[k][i];
+                    const float h = (float)v;
+                    ff[i] = make_float2(h, std::isfinite(v) ? (float)(v - (double)h) : 0.0f);
+                }
+                ce = up(p->lnmu_ff[k], ff.data(), sizeof(float2) * N[k]);
+                // the staging vector must outlive the copy
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->st);
+            }
+        }
+        // the staging vectors above go out of scope: wait for their copies
+        ce = ce ? ce : cudaStreamSynchronize(p->st);
     }
     // carries of the empty state are never written by the level scans
     ce = ce ? ce : cudaMemsetAsync(p->fcarry, 0, (size_t)nt * p->NS * p->sfsz, p->st);
@@ -1227,6 +1334,14 @@ mmot_status mmot_reset_potentials(mmot_plan p)
     CUDA_TRY(cudaMemcpyAsync(p->beta, p->h_beta.data(), sizeof(double) * p->h_beta.size(),
                              cudaMemcpyHostToDevice, p->st));
     CUDA_TRY(cudaMemsetAsync(p->lphi, 0, (size_t)p->T * p->esz, p->st));
+    if (p->three_phase) {
+        if (p->esz == 8)
+            k_fill<double><<<256, 256, 0, p->st>>>(static_cast<double *>(p->ephi), p->Tpad, 1.0);
+        else
+            k_fill<float><<<256, 256, 0, p->st>>>(static_cast<float *>(p->ephi), p->Tpad, 1.0f);
+        CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
+    }
     p->ops_target = -1;
     return MMOT_OK;
 }

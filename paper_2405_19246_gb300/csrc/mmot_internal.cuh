@@ -55,6 +55,14 @@ struct SweepArgs {
     const int32_t *cnt;       // [nt*l] points of marginal m before tile b
     const int32_t *reftile;   // [nt*l] tile whose beta represents marginal m in tile b
     double *beta;             // [nt*l] per-tile baseline of g_m/eps
+    // the same points in the padded stream of the tile kernels (l <= 5):
+    // tile b occupies [toff[b], toff[b] + n_b), toff[b] a multiple of 16;
+    // FP32 or FP64 values
+    const uint32_t *toff;     // [nt] stream offset of each tile
+    const void *epos;         // e^{(x_t - x_first_of_tile)/eps}
+    void *ephi;               // e^{g_m(i)/eps - beta[b*l+m]}
+    const uint8_t *emid;      // marginal of the point, 0xff for padding
+    const float2 *lnmuj_ff;   // [N_j] ln mu_j as FP32 hi + lo (FP32 path)
     // per merged point
     // FP32 arrays for the FP32 path, FP64 arrays for the all-FP64 path
     const void *pos;          // (x_t - xlb[b])/eps

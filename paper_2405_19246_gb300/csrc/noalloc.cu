@@ -10,8 +10,9 @@
 // exits.
 //
 // The computation is the same as mmot_marginal on a plan (FP32 in-tile scans,
-// three-phase tile operators / carry scan / tile products): merge and tiling
-// on the host, tables copied into the static scratch, three kernel launches.
+// three-phase tile operators / carry scan / tile products): merge, tiling and
+// the padded exponential stream on the host, tables copied into the static
+// scratch, three kernel launches.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -171,12 +172,27 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
         }
     for (double &bq : beta)
         if (!std::isfinite(bq)) bq = 0.0;
-    std::vector<float> hpos(T), hlphi(T);
-    for (int64_t t = 0; t < T; ++t) hpos[t] = (float)L.pos[t];
+    // padded stream of the tile kernels: every tile starts on a 16-element
+    // boundary; e^{pos}, scaled phi e^{g/eps - beta}, marginal (0xff: padding)
+    std::vector<uint32_t> htoff(nt);
+    int64_t Tp = 0;
+    for (int b = 0; b < nt; ++b) {
+        htoff[b] = (uint32_t)Tp;
+        Tp += ((int64_t)(L.tstart[b + 1] - L.tstart[b]) + 15) / 16 * 16;
+    }
+    std::vector<float> hepos(Tp, 1.0f), hephi(Tp, 0.0f);
+    std::vector<uint8_t> hemid(Tp, 0xff);
+    for (int b = 0; b < nt; ++b)
+        for (uint32_t t = L.tstart[b]; t < L.tstart[b + 1]; ++t) {
+            const size_t u = (size_t)htoff[b] + (t - L.tstart[b]);
+            hepos[u] = (float)std::exp(L.pos[t]);
+            hemid[u] = L.mid[t];
+        }
     for (int q = 0; q < l; ++q)
         for (int64_t i = 0; i < N[q]; ++i) {
             const uint32_t t = L.mpos[q][i];
-            hlphi[t] = (float)(hg[q][i] / eps - beta[(size_t)L.tile_of[t] * l + q]);
+            const uint32_t b = L.tile_of[t];
+            hephi[(size_t)htoff[b] + (t - L.tstart[b])] = (float)std::exp(hg[q][i] / eps - beta[(size_t)b * l + q]);
         }
     std::vector<unsigned char> decF, decB;
     decay_tables(L, NB, false, decF, decB);
@@ -188,9 +204,10 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
         off = align256(off + bytes);
         return o;
     };
-    const size_t o_pos = take(sizeof(float) * T);
-    const size_t o_lphi = take(sizeof(float) * T);
-    const size_t o_mid = take((size_t)T);
+    const size_t o_epos = take(sizeof(float) * Tp);
+    const size_t o_ephi = take(sizeof(float) * Tp);
+    const size_t o_emid = take((size_t)Tp);
+    const size_t o_toff = take(sizeof(uint32_t) * nt);
     const size_t o_ts = take(sizeof(uint32_t) * (nt + 1));
     const size_t o_ulb = take(sizeof(double) * nt);
     const size_t o_urb = take(sizeof(double) * nt);
@@ -210,9 +227,10 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     if (off > kScratchBytes) return err_msg(MMOT_ERR_RANGE, "problem needs %zu scratch bytes > %zu", off, kScratchBytes);
     std::vector<unsigned char> stage(o_opF, 0);   // everything the host fills
     auto put = [&](size_t o, const void *src, size_t bytes) { std::memcpy(stage.data() + o, src, bytes); };
-    put(o_pos, hpos.data(), sizeof(float) * T);
-    put(o_lphi, hlphi.data(), sizeof(float) * T);
-    put(o_mid, L.mid.data(), (size_t)T);
+    put(o_epos, hepos.data(), sizeof(float) * Tp);
+    put(o_ephi, hephi.data(), sizeof(float) * Tp);
+    put(o_emid, hemid.data(), (size_t)Tp);
+    put(o_toff, htoff.data(), sizeof(uint32_t) * nt);
     put(o_ts, L.tstart.data(), sizeof(uint32_t) * (nt + 1));
     put(o_ulb, L.ulb.data(), sizeof(double) * nt);
     put(o_urb, L.urb.data(), sizeof(double) * nt);
@@ -245,9 +263,10 @@ extern "C" mmot_status mmot_marginal_noalloc(int l, const int64_t *N, const doub
     a.cnt = reinterpret_cast<const int32_t *>(scratch + o_cnt);
     a.reftile = reinterpret_cast<const int32_t *>(scratch + o_ref);
     a.beta = reinterpret_cast<double *>(scratch + o_beta);
-    a.pos = scratch + o_pos;
-    a.mid = scratch + o_mid;
-    a.lphi = scratch + o_lphi;
+    a.epos = scratch + o_epos;
+    a.ephi = scratch + o_ephi;
+    a.emid = scratch + o_emid;
+    a.toff = reinterpret_cast<const uint32_t *>(scratch + o_toff);
     a.opF = scratch + o_opF;
     a.opB = scratch + o_opB;
     a.fcarry = scratch + o_fc;

@@ -3,6 +3,7 @@
 #include "shapes.cuh"
 #include "sweep.cuh"
 #include "warp.cuh"
+#include "tile.cuh"
 
 // launchers of the three-phase design, defined for NB <= kMaxOpBits
 #define MMOT_INSTANTIATE_OPS(NB_, V_)                                                  \
@@ -11,13 +12,13 @@
     cudaError_t launch_tileop<NB_, V_>(const SweepArgs &a, cudaStream_t s)             \
     {                                                                                  \
         using S = Shape<NB_, V_>;                                                      \
-        return launch_tileop_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                \
+        return launch_tops_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                  \
     }                                                                                  \
     template <>                                                                        \
     cudaError_t launch_prod<NB_, V_>(const SweepArgs &a, cudaStream_t s)               \
     {                                                                                  \
         using S = Shape<NB_, V_>;                                                      \
-        return launch_prod_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                  \
+        return launch_tile_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                  \
     }                                                                                  \
     template <>                                                                        \
     cudaError_t launch_carry<NB_, V_>(const SweepArgs &a, cudaStream_t s)              \

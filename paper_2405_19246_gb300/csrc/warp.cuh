@@ -27,6 +27,7 @@ namespace mmot {
 // for the all-subset sweeps of the objective).
 template <int NB, typename V, int LM = NB + 1>
 struct WarpRun {
+    static_assert(NB + 1 <= 16, "a row of the factor buffer holds levels 0..NB");
     static constexpr int NS = 1 << NB;
     static constexpr int NQ = NS / 32;
     static constexpr int L = LM;
@@ -63,24 +64,78 @@ struct WarpRun {
         return s;
     }
 
+    // gamma_s for a runtime level (selected from registers: no local memory)
+    __device__ double gam_at(int s) const
+    {
+        double g = 0.0;
+#pragma unroll
+        for (int q = 0; q <= NB; ++q)
+            if (q == s) g = gam[q];
+        return g;
+    }
+
     // states from absolute carries (levels below maxlev; the rest 0)
     __device__ void load_carries(const SfT<V> *carry, int b, const double *beta, int maxlev)
     {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int T = lane + 32 * q;
-            const int s = popc_c(T);
+            const int s = __popc(T);
             f[q] = sf_zero<V>();
             if (T != 0 && s < maxlev)
-                f[q] = sf_scale_exp(sf_load<V>(carry[(size_t)b * NS + T]), -(sum_beta(beta, T) + gam[s]));
+                f[q] = sf_scale_exp(sf_load<V>(carry[(size_t)b * NS + T]), -(sum_beta(beta, T) + gam_at(s)));
+        }
+    }
+
+    // Injection factors of the chunk's points, one point per lane, all levels:
+    // fb[lane][s] = exp(ln phi + a_s p - D_s), a_s = w_s - w_{s-1}
+    __device__ void chunk_facs(V lp, V pp, bool inj, V (*fb)[16]) const
+    {
+        if (inj) {
+            static_for<1, NB + 1>([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                fb[lane][s] = vexp<V>(lp + (V)(rate(s) - rate(s - 1)) * pp - D[s]);
+            });
+        }
+        __syncwarp();
+    }
+
+    // F_T += phi F_{T\k} for every state T containing k, factors fr[s] of the
+    // point (F_{T\k} sits in lane ^ 2^k for k < 5, in register q ^ 2^{k-5}
+    // otherwise; the empty state is 1)
+    __device__ __forceinline__ void inject(int k, const V *fr)
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int T = lane + 32 * q;
+            Sf<V> src;
+            if (k < 5) {
+                src.m = __shfl_xor_sync(FULL, f[q].m, 1 << k);
+                src.k = __shfl_xor_sync(FULL, f[q].k, 1 << k);
+            } else {
+                src = f[0];
+#pragma unroll
+                for (int q2 = 0; q2 < NQ; ++q2)
+                    if (q2 == (q ^ (1 << (k - 5)))) src = f[q2];
+            }
+            if ((T >> k) & 1) {
+                if ((T ^ (1 << k)) == 0) src = Sf<V>{V(0.5), 1};
+                if (src.m != V(0)) {
+                    Sf<V> t = sf_make<V>(src.m * fr[__popc(T)]);
+                    t.k += src.k;
+                    if (t.m != V(0)) f[q] = sf_add(f[q], t);
+                }
+            }
         }
     }
 
     // Walk the tile's n points in processing order; on_target(slot, p) at the
     // target points with the states before the point.  bits of the marginals:
-    // m < j -> m, m > j -> m - 1, target j -> -1.
+    // m < j -> m, m > j -> m - 1, target j -> -1.  fb: this warp's 32 x 16
+    // buffer of injection factors (shared memory).
     template <typename OnT>
-    __device__ void run(const SweepArgs &a, uint32_t t0, int n, int j, bool fwd, int ntarget, OnT &&on_target)
+    __device__ void run(const SweepArgs &a, uint32_t t0, int n, int j, bool fwd, int ntarget, V (*fb)[16],
+                        OnT &&on_target)
     {
         const V *pos = static_cast<const V *>(a.pos);
         const V *lphi = static_cast<const V *>(a.lphi);
@@ -97,48 +152,20 @@ struct WarpRun {
                 pp = fwd ? x : span - x;
                 lp = lphi[t0 + id];
             }
+            chunk_facs(lp, pp, bit >= 0, fb);
             const int cnt = min(32, n - c0);
             for (int i = 0; i < cnt; ++i) {
                 const int k = __shfl_sync(FULL, bit, i);
-                const V p = __shfl_sync(FULL, pp, i);
                 if (k == -1) {
+                    const V p = __shfl_sync(FULL, pp, i);
                     const int slot = fwd ? seen : ntarget - 1 - seen;
                     on_target(slot, p);
                     ++seen;
                     continue;
                 }
-                const V l = __shfl_sync(FULL, lp, i);
-                // injection factor of level lane+1 in lane lane (level s = |T|)
-                V facl = V(0);
-                if (lane < NB) {
-                    const int s = lane + 1;
-                    facl = vexp<V>(l + (V)(rate(s) - rate(s - 1)) * p - D[s]);
-                }
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const int T = lane + 32 * q;
-                    const V fac = __shfl_sync(FULL, facl, (popc_c(T) + 31) & 31);
-                    Sf<V> src;
-                    if (k < 5) {
-                        src.m = __shfl_xor_sync(FULL, f[q].m, 1 << k);
-                        src.k = __shfl_xor_sync(FULL, f[q].k, 1 << k);
-                    } else {
-                        src = f[0];
-#pragma unroll
-                        for (int q2 = 0; q2 < NQ; ++q2)
-                            if (q2 == (q ^ (1 << (k - 5)))) src = f[q2];
-                    }
-                    if ((T >> k) & 1) {
-                        // F_{T\k}, with the empty state equal to 1
-                        if ((T ^ (1 << k)) == 0) src = Sf<V>{V(0.5), 1};
-                        if (src.m != V(0)) {
-                            Sf<V> t = sf_make<V>(src.m * fac);
-                            t.k += src.k;
-                            if (t.m != V(0)) f[q] = sf_add(f[q], t);
-                        }
-                    }
-                }
+                inject(k, fb[i]);
             }
+            __syncwarp();   // the next chunk overwrites fb
         }
     }
 };
@@ -149,10 +176,9 @@ struct WarpRun {
 // walked (position = index forward, n - 1 - index backward).
 template <int NB, typename V, int LM, bool PRE, typename OnP>
 __device__ void warp_run_each(WarpRun<NB, V, LM> &r, const SweepArgs &a, uint32_t t0, int n, bool fwd,
-                              int r0, int r1, OnP &&on_point)
+                              int r0, int r1, V (*fb)[16], OnP &&on_point)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int NQ = WarpRun<NB, V, LM>::NQ;
     const V *pos = static_cast<const V *>(a.pos);
     const V *lphi = static_cast<const V *>(a.lphi);
     const int lane = r.lane;
@@ -167,43 +193,17 @@ __device__ void warp_run_each(WarpRun<NB, V, LM> &r, const SweepArgs &a, uint32_
             pp = fwd ? x : r.span - x;
             lp = lphi[t0 + idl];
         }
+        r.chunk_facs(lp, pp, bit >= 0, fb);
         const int cnt = min(32, r1 - c0);
         for (int i = 0; i < cnt; ++i) {
             const int k = __shfl_sync(FULL, bit, i);
             const V p = __shfl_sync(FULL, pp, i);
             const int id = __shfl_sync(FULL, idl, i);
             if constexpr (PRE) on_point(id, p);
-            const V l = __shfl_sync(FULL, lp, i);
-            V facl = V(0);
-            if (lane < NB) {
-                const int s = lane + 1;
-                facl = vexp<V>(l + (V)(r.rate(s) - r.rate(s - 1)) * p - r.D[s]);
-            }
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int T = lane + 32 * q;
-                const V fac = __shfl_sync(FULL, facl, (popc_c(T) + 31) & 31);
-                Sf<V> src;
-                if (k < 5) {
-                    src.m = __shfl_xor_sync(FULL, r.f[q].m, 1 << k);
-                    src.k = __shfl_xor_sync(FULL, r.f[q].k, 1 << k);
-                } else {
-                    src = r.f[0];
-#pragma unroll
-                    for (int q2 = 0; q2 < NQ; ++q2)
-                        if (q2 == (q ^ (1 << (k - 5)))) src = r.f[q2];
-                }
-                if ((T >> k) & 1) {
-                    if ((T ^ (1 << k)) == 0) src = Sf<V>{V(0.5), 1};
-                    if (src.m != V(0)) {
-                        Sf<V> t = sf_make<V>(src.m * fac);
-                        t.k += src.k;
-                        if (t.m != V(0)) r.f[q] = sf_add(r.f[q], t);
-                    }
-                }
-            }
+            r.inject(k, fb[i]);
             if constexpr (!PRE) on_point(id, p);
         }
+        __syncwarp();
     }
 }
 
@@ -241,16 +241,17 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
     const int n = (int)(a.tstart[b + 1] - t0);
     double beta[NB];
     warp_betas(a, b, a.j, NB, beta);
+    __shared__ V fbuf[4][32][16];
     WarpRun<NB, V, LM> r;
     r.init(a, b);
     r.load_carries(sfp<V>(fwd ? a.fcarry : a.bcarry), b, beta, SL);
-    r.run(a, t0, n, a.j, fwd, 0, [](int, V) {});
+    r.run(a, t0, n, a.j, fwd, 0, fbuf[threadIdx.x >> 5], [](int, V) {});
 #pragma unroll
     for (int q = 0; q < WarpRun<NB, V, LM>::NQ; ++q) {
         const int T = r.lane + 32 * q;
         if (popc_c(T) == SL)
             sfp<V>(a.agg)[(size_t)b * NS + T] =
-                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V, LM>::sum_beta(beta, T) + r.gam[SL]));
+                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V, LM>::sum_beta(beta, T) + r.gam_at(SL)));
     }
 }
 
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ SfT<V> Gt[JCAP * NS];
     __shared__ double gq[JCAP];
+    __shared__ V fbuf[32][16];
     const int b = blockIdx.x;
     if (a.frozen && (a.mode == MODE_UPDATE || a.mode == MODE_RESIDUAL) && a.frozen[a.seg[b]]) {
         if (a.mode == MODE_RESIDUAL && threadIdx.x == 0) a.partial[b] = 0.0;
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     R rb;
     rb.init(a, b);
     rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
-    rb.run(a, t0, n, a.j, false, nt, [&](int slot, V) {
+    rb.run(a, t0, n, a.j, false, nt, fbuf, [&](int slot, V) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) Gt[slot * NS + lane + 32 * q] = sf_store(rb.f[q]);
     });
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     V qmax = V(-INFINITY);
     bool bad = false;
     double racc = 0.0;
-    rf.run(a, t0, n, a.j, true, nt, [&](int slot, V pF) {
+    rf.run(a, t0, n, a.j, true, nt, fbuf, [&](int slot, V pF) {
         const V pG = rb.span - pF;
         // per-level factor exp(gamma^F_s + gamma^G_{NB-s} - w_s pF - w_{NB-s} pG)
         // as 2^(n_s) * mu_s, computed by lane s
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
         V em = V(0);
         if (lane <= NB) {
             const int s = lane;
-            const double c = (rf.gam[s] + rb.gam[NB - s] - (double)R::rate(s) * (double)pF -
+            const double c = (rf.gam_at(s) + rb.gam_at(NB - s) - (double)R::rate(s) * (double)pF -
                               (double)R::rate(NB - s) * (double)pG) * kLog2e;
             const double fl = floor(c);
             en = (int)fl;
@@ -375,22 +377,31 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
             }
         }
     });
-    if (lane == 0) {
-        if (a.mode == MODE_UPDATE) {
+    if (a.mode == MODE_UPDATE) {
+        // new potentials and ln phi relative to the new baseline, by lane
+        // (each lane its points; the slot is the rank among the targets)
+        const double bx = isfinite((double)__shfl_sync(FULL, qmax, 0)) ? (double)__shfl_sync(FULL, qmax, 0) : 0.0;
+        if (lane == 0) {
             if (bad) atomicOr(a.err, ERR_NONFINITE);
-            const double bx = isfinite((double)qmax) ? (double)qmax : 0.0;
             if (nt > 0) a.beta[(size_t)b * a.l + a.j] = bx;
-            V *lph = static_cast<V *>(a.lphi);
-            for (int slot = 0, r = 0; r < n; ++r) {
-                if (a.mid[t0 + r] != a.j) continue;
+        }
+        __syncwarp();
+        V *lph = static_cast<V *>(a.lphi);
+        int base = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int r = c0 + lane;
+            const bool tg = (r < n) && (a.mid[t0 + r] == a.j);
+            const unsigned mask = __ballot_sync(FULL, tg);
+            if (tg) {
+                const int slot = base + __popc(mask & ((1u << lane) - 1u));
                 const double g = gq[slot];
                 a.gj[off + slot] = eps_b * g;
                 lph[t0 + r] = (V)(g - bx);
-                ++slot;
             }
-        } else if (a.mode == MODE_RESIDUAL) {
-            a.partial[b] = racc;
+            base += __popc(mask);
         }
+    } else if (a.mode == MODE_RESIDUAL) {
+        if (lane == 0) a.partial[b] = racc;
     }
 }
 
@@ -417,6 +428,7 @@ __global__ void __launch_bounds__(32) k_wobj(SweepArgs a)
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char wsm[];
     SfT<V> *Gall = reinterpret_cast<SfT<V> *>(wsm);
+    __shared__ V fbuf[32][16];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t t0 = a.tstart[b];
@@ -437,7 +449,7 @@ __global__ void __launch_bounds__(32) k_wobj(SweepArgs a)
     V em = V(0);
     if (lane <= NB) {
         const int s = lane;
-        const double c = (rf.gam[s] + rb.gam[NB - s] - (double)R::rate(s) * (double)rf.span) * kLog2e;
+        const double c = (rf.gam_at(s) + rb.gam_at(NB - s) - (double)R::rate(s) * (double)rf.span) * kLog2e;
         const double fl = floor(c);
         en = (int)fl;
         em = vexp2<V>((V)(c - fl));
@@ -451,14 +463,14 @@ __global__ void __launch_bounds__(32) k_wobj(SweepArgs a)
     // backward states including each point of [c0, c1)
     rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
     __syncwarp();
-    warp_run_each<NB, V, NB, false>(rb, a, t0, n, false, 0, n - c0, [&](int id, V) {
+    warp_run_each<NB, V, NB, false>(rb, a, t0, n, false, 0, n - c0, fbuf, [&](int id, V) {
         if (id < c1) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Gall[(size_t)(id - c0) * NS + lane + 32 * q] = sf_store(rb.f[q]);
         }
     });
     __syncwarp();
-    warp_run_each<NB, V, NB, true>(rf, a, t0, n, true, c0, c1, [&](int id, V) {
+    warp_run_each<NB, V, NB, true>(rf, a, t0, n, true, c0, c1, fbuf, [&](int id, V) {
         int Emax = INT_MIN / 2;
         V sw = V(0), sz = V(0);
 #pragma unroll
