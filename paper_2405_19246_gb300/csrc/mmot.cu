@@ -191,6 +191,8 @@ struct mmot_plan_s {
     bool three_phase = false;  // tile operators + carry scan (l <= 5)
     int ops_target = -1;       // target whose tile operators are current
     double *partial = nullptr;
+    double *part4 = nullptr;   // [nt*4] per-tile objective sums
+    double *d_obj = nullptr;   // [nseg*5] per instance: mass, residual, primal, g mu, W
     int *flags = nullptr;   // flags followed by the tile counter
     size_t flags_bytes = 0;
     int *err = nullptr;
@@ -331,6 +333,16 @@ void shape_nb(bool fp64, int *K, int *NT, int *JCAP)
     }
 }
 
+int tile_jcap(int NB, bool fp64)
+{
+    switch (NB) {
+    case 1: return fp64 ? TShape<1, double>::JCAP : TShape<1, float>::JCAP;
+    case 2: return fp64 ? TShape<2, double>::JCAP : TShape<2, float>::JCAP;
+    case 3: return fp64 ? TShape<3, double>::JCAP : TShape<3, float>::JCAP;
+    default: return fp64 ? TShape<4, double>::JCAP : TShape<4, float>::JCAP;
+    }
+}
+
 void shape_of(int NB, bool fp64, int *K, int *NT, int *JCAP)
 {
     switch (NB) {
@@ -390,6 +402,7 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.muj = (j < p->l) ? p->mu[j] : nullptr;
     a.out = out;
     a.partial = p->partial;
+    a.part4 = p->part4;
     a.err = p->err;
     a.seg = p->d_seg;
     a.teps = p->d_teps;
@@ -401,7 +414,7 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
 // (three-phase, l <= 5), or 2 (NB levels x contribution + scan) + products
 int launches_per_product(mmot_plan p) { return p->three_phase ? 2 : 4 * p->NB + 1; }
 
-// kernel ids: 2 k_tileop, 3 k_carry, 4 k_prod (three-phase design, l <= 5);
+// kernel ids: 2 k_tops, 3 k_carry, 4 k_tile (three-phase design, l <= 5);
 // 5 k_wpass, 6 k_lscan, 4 k_wprod (level passes and warp tiles, l >= 6);
 // 0, 1 are not used by marginal products (objective sweeps only)
 mmot_status timed_launch(mmot_plan p, int kernel, const SweepArgs &a, bool fp64, int SL = 0, int fwd = 0)
@@ -601,6 +614,52 @@ __global__ void k_reset_seg(double *g, const int64_t *off, const double *g0, int
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) g[i] = v;
 }
 
+// Objective sums of instance q (one block each), compensated (Kahan) over
+// the instance's tiles: from part4 (per tile: plan-marginal mass, L1 error,
+// sum g marg, sum g mu of one marginal) into acc[q*5 + 0..3] (the mass is
+// set, the others accumulate over the marginals), or, with w_lnz, the
+// transport cost W = Z * sum of the per-tile W_b / Z_b (partial) into
+// acc[q*5 + 4], Z from ln Z of the instance's first tile.
+__global__ void k_seg_obj(const double *part4, const double *partial, const double *w_lnz, const int32_t *t0,
+                          double *acc, int set_mass)
+{
+    const int q = blockIdx.x;
+    const int b0 = t0[q], b1 = t0[q + 1];
+    const int NQ = w_lnz ? 1 : 4;
+    __shared__ double s_s[4][256], s_c[4][256];
+    for (int m = 0; m < NQ; ++m) {
+        double sum = 0.0, c = 0.0;
+        for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
+            const double y = (w_lnz ? partial[b] : part4[(size_t)b * 4 + m]) - c;
+            const double t = sum + y;
+            c = (t - sum) - y;
+            sum = t;
+        }
+        s_s[m][threadIdx.x] = sum;
+        s_c[m][threadIdx.x] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int m = 0; m < NQ; ++m) {
+            double S = 0.0, Cc = 0.0;
+            for (int i = 0; i < (int)blockDim.x; ++i) {
+                const double y = s_s[m][i] - s_c[m][i] - Cc;
+                const double t = S + y;
+                Cc = (t - S) - y;
+                S = t;
+            }
+            if (w_lnz) {
+                const double lz = w_lnz[b0];
+                acc[(size_t)q * 5 + 4] = (lz == -INFINITY) ? 0.0 : S * exp(lz);
+            } else if (m == 0) {
+                if (set_mass) acc[(size_t)q * 5 + 0] = S;
+            } else {
+                acc[(size_t)q * 5 + m] += S;
+            }
+        }
+    }
+}
+
 // res[q] (+)= sum of the per-tile partial sums of instance q (one thread per
 // instance, compensated)
 __global__ void k_seg_sum(const double *partial, const int32_t *t0, int nseg, double *res, int accumulate)
@@ -765,6 +824,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     const bool fp64 = (prec == MMOT_FP64);
     int K = 0, NT = 0, jcap = 0;
     shape_of(l - 1, fp64, &K, &NT, &jcap);
+    if (l - 1 <= kMaxOpBits) jcap = tile_jcap(l - 1, fp64);   // the tile kernels' target capacity
     if (l - 1 > kMaxOpBits) {
         // warp-tile products (warp.cuh)
         K = fp64 ? wshape_k<double>(l - 1) : wshape_k<float>(l - 1);
@@ -939,6 +999,9 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
             for (int k = 0; k < l; ++k) PA(p->lnmu_ff[k], N[k]);
     }
     PA(p->partial, nt);
+    PA(p->part4, (size_t)nt * 4);
+    PA(p->d_obj, (size_t)nin * 5);
+    if (!batch) PA(p->d_segt0, 2);
     p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);
     PA(p->flags, (size_t)nt * (p->NB + 1) + 1);
     PA(p->err, 1);
@@ -1003,7 +1066,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
             for (int k = 0; k < l; ++k) g0[(size_t)q * l + k] = -ins[q].eps * std::log((double)ins[q].N[k]);
         ce = ce ? ce : up(p->d_seg, hseg.data(), sizeof(int32_t) * nt);
         ce = ce ? ce : up(p->d_teps, hteps.data(), sizeof(double) * nt);
-        ce = ce ? ce : up(p->d_segt0, seg_tile0.data(), sizeof(int32_t) * (nin + 1));
+
         ce = ce ? ce : up(p->d_goff, seg_off.data(), sizeof(int64_t) * seg_off.size());
         ce = ce ? ce : up(p->d_g0, g0.data(), sizeof(double) * g0.size());
         ce = ce ? ce : cudaMemsetAsync(p->d_frozen, 0, sizeof(int32_t) * nin, p->st);
@@ -1056,6 +1119,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         // the staging vectors above go out of scope: wait for their copies
         ce = ce ? ce : cudaStreamSynchronize(p->st);
     }
+    ce = ce ? ce : up(p->d_segt0, seg_tile0.data(), sizeof(int32_t) * (nin + 1));
     // carries of the empty state are never written by the level scans
     ce = ce ? ce : cudaMemsetAsync(p->fcarry, 0, (size_t)nt * p->NS * p->sfsz, p->st);
     ce = ce ? ce : cudaMemsetAsync(p->bcarry, 0, (size_t)nt * p->NS * p->sfsz, p->st);
@@ -1071,58 +1135,42 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
 
 // Objective terms of every instance of a plan (one for a single problem):
 // residual over all l marginals, W, primal, dual and mass (Eq. k-mmot
-// distance), from one plan-marginal product per marginal and the objective
-// sweeps.
+// distance).  One product per marginal sums its terms per tile on the device
+// (FP64), a compensated per-instance reduction follows, and the transport cost
+// comes from the objective sweeps; only five FP64 values per instance reach
+// the host.
 mmot_status plan_objective(mmot_plan p, std::vector<mmot_result> &R)
 {
     const int l = p->l, ns = p->nseg;
     R.assign(ns, mmot_result{});
-    std::vector<double> Z(ns, 0.0), P(ns, 0.0), D(ns, 0.0), res(ns, 0.0);
+    CUDA_TRY(cudaMemsetAsync(p->d_obj, 0, sizeof(double) * 5 * ns, p->st));
     for (int k = 0; k < l; ++k) {
-        std::vector<double> marg(p->N[k]), g(p->N[k]), m(p->N[k]);
-        mmot_status s = mmot_marginal(p, k, 1, marg.data());
+        mmot_status s = enqueue_product(p, k, MODE_OBJ, nullptr);
         if (s != MMOT_OK) return s;
-        CUDA_TRY(cudaMemcpy(g.data(), p->g[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
-        CUDA_TRY(cudaMemcpy(m.data(), p->mu[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost));
-        for (int q = 0; q < ns; ++q) {
-            double z = 0.0;
-            for (int64_t i = p->seg_off[(size_t)q * l + k]; i < p->seg_off[(size_t)(q + 1) * l + k]; ++i) {
-                z += marg[i];
-                res[q] += std::fabs(marg[i] - m[i]);
-                if (std::isfinite(g[i])) {
-                    P[q] += g[i] * marg[i];
-                    D[q] += g[i] * m[i];
-                }
-            }
-            if (k == l - 1) Z[q] = z;
-        }
+        k_seg_obj<<<ns, 256, 0, p->st>>>(p->part4, nullptr, nullptr, p->d_segt0, p->d_obj, k == l - 1);
+        CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
     }
-    for (int q = 0; q < ns; ++q) {
-        const double e = p->seg_eps[q];
-        R[q].residual = res[q];
-        R[q].mass = Z[q];
-        R[q].primal = P[q];
-        R[q].dual = D[q] + e - e * Z[q];
-        R[q].W = NAN;
+    const bool with_w = (l <= kMaxObjectiveL);
+    if (with_w) {
+        // transport cost: per instance, Z times the sum over its tiles of eps W_b / Z_b
+        mmot_status sc = enqueue_cost(p);
+        if (sc != MMOT_OK) return sc;
+        k_seg_obj<<<ns, 256, 0, p->st>>>(nullptr, p->partial, p->o_lnz, p->d_segt0, p->d_obj, 0);
+        CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
     }
-    if (l > kMaxObjectiveL) return check_device_error(p);
-    // transport cost: per instance, Z times the sum over its tiles of eps W_b / Z_b
-    mmot_status sc = enqueue_cost(p);
-    if (sc != MMOT_OK) return sc;
-    std::vector<double> part(p->nt), lnz(p->nt);
-    CUDA_TRY(cudaMemcpyAsync(part.data(), p->partial, sizeof(double) * p->nt, cudaMemcpyDeviceToHost, p->st));
-    CUDA_TRY(cudaMemcpyAsync(lnz.data(), p->o_lnz, sizeof(double) * p->nt, cudaMemcpyDeviceToHost, p->st));
+    std::vector<double> h((size_t)ns * 5);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), p->d_obj, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, p->st));
     CUDA_TRY(cudaStreamSynchronize(p->st));
     for (int q = 0; q < ns; ++q) {
-        double sum = 0.0, c = 0.0;
-        for (int b = p->seg_tile0[q]; b < p->seg_tile0[q + 1]; ++b) {
-            const double y = part[b] - c;
-            const double t = sum + y;
-            c = (t - sum) - y;
-            sum = t;
-        }
-        const double lz = lnz[p->seg_tile0[q]];
-        R[q].W = (lz == -INFINITY) ? 0.0 : sum * std::exp(lz);
+        const double e = p->seg_eps[q];
+        const double *o = &h[(size_t)q * 5];
+        R[q].mass = o[0];
+        R[q].residual = o[1];
+        R[q].primal = o[2];
+        R[q].dual = o[3] + e - e * o[0];
+        R[q].W = with_w ? o[4] : NAN;
     }
     return check_device_error(p);
 }

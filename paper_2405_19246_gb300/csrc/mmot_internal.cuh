@@ -29,6 +29,7 @@ enum Mode : int {
     MODE_OUT_PLAN = 2,     // out[i] = phi_j(i) M_j(i)
     MODE_OUT_LNM = 3,      // out[i] = ln M_j(i)
     MODE_RESIDUAL = 4,     // partial[b] = sum over tile of |phi_j M_j - mu_j|
+    MODE_OBJ = 5,          // part4[b] = tile sums of marg_j, |marg_j - mu_j|, g_j marg_j, g_j mu_j
 };
 
 enum ErrBits : int {
@@ -95,6 +96,7 @@ struct SweepArgs {
     const double *muj;        // [N_j] mu_j
     double *out;              // [N_j] output for the OUT modes
     double *partial;          // [nt] per-tile residual sums
+    double *part4;            // [nt*4] per-tile objective sums (MODE_OBJ)
     int *err;                 // error bits
     // batches of independent instances (all NULL for a single instance):
     // tiles never straddle two instances and no state crosses a boundary

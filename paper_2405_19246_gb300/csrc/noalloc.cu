@@ -47,8 +47,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 template <int NB>
 void shape_f32(int *K, int *jcap)
 {
-    *K = Shape<NB, float>::K;
-    *jcap = Shape<NB, float>::JCAP;
+    *K = TShape<NB, float>::K;
+    *jcap = TShape<NB, float>::JCAP;
 }
 
 mmot_status err_msg(mmot_status st, const char *fmt, ...)

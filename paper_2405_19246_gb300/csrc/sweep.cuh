@@ -14,24 +14,21 @@
 // multipliers moved into the frame.
 //
 // Block engine (Engine, one tile per CTA, each thread a contiguous chunk of
-// points; l <= 5).  Level s = |T| depends on level s-1 at the same point, so a
-// tile runs level by level: walk the points recomputing levels 1..s from the
-// final lower-level values, block-scan the level-s chunk totals, take the
-// level's carries, then give every state of the level its own scale (the
-// largest tile-end value of the state becomes 1).  Values inside a tile are
-// FP32 (or FP64) "f-representations" F~_S exp(-sum_{m in S} beta_m) / scale_S
-// with per-tile FP64 baselines beta_m (the re-centring of Algorithm 5).
-// Carries between tiles are scaled floats (mantissa, binary exponent).
+// points).  Level s = |T| depends on level s-1 at the same point, so a tile
+// runs level by level: walk the points recomputing levels 1..s from the final
+// lower-level values, block-scan the level-s chunk totals, take the level's
+// carries, then give every state of the level its own scale (the largest
+// tile-end value of the state becomes 1).  Values inside a tile are FP32 (or
+// FP64) "f-representations" F~_S exp(-sum_{m in S} beta_m) / scale_S with
+// per-tile FP64 baselines beta_m (the re-centring of Algorithm 5).  Carries
+// between tiles are scaled floats (mantissa, binary exponent).
 //
-// Three-phase product (l <= 5): k_tileop computes every tile's carry-free
-// transfer operator, k_carry scans the operators over the tiles for the exact
-// carries, k_prod recomputes each tile from its forward and backward carries,
-// keeps the backward states at the target points in shared memory, combines
-//     M_j(i) = sum_S F_S(x_i^-) G_{R\S}(x_i^+)
-// at the target points and applies the FP64 epilogue (potential update
-// g_j = eps (ln mu_j - ln M_j), residual, or an output mode).  Products with
-// l >= 6 use warp tiles and level passes (warp.cuh); the look-back scan of
-// the Engine (lookback, k_bwd) serves the objective sweeps (objective.cuh).
+// This engine serves the objective sweeps over all 2^l subsets
+// (objective.cuh): tile operators (k_tileop) and the multi-block carry scan
+// (k_carry) for l <= 4, the look-back scan (lookback, k_bwd) for l = 5..7.
+// The carry scan also serves the marginal products of l <= 5, whose tile
+// kernels are in tile.cuh; the products of l >= 6 run in warp.cuh with the
+// level scans (k_lscan) defined here.
 #pragma once
 #include <limits>
 #include <climits>
@@ -953,369 +950,6 @@ __global__ void __launch_bounds__(NT, 3) k_bwd(SweepArgs a)
         sfp<V>(a.bcarry)[(size_t)b * NS + S] = (S == 0) ? sf_one_st<V>() : sf_store(sm.E[S]);
 }
 
-// One tile of a marginal product: backward states from the stored carry,
-// forward states (look-back when LOOKBACK, else from the stored forward carry),
-// combine at the target points and the FP64 epilogue.
-template <int NB, typename V, int NT, int C, int JCAP, bool LOOKBACK>
-__device__ void product_body(SweepSmem<NB, V, NT, C, JCAP, true> &sm, const SweepArgs &a, int v, int b)
-{
-    using En = Engine<NB, V, NT, C, JCAP, true>;
-    constexpr int NS = 1 << NB;
-    constexpr int FULLS = NS - 1;
-    constexpr unsigned FULL = 0xffffffffu;
-    constexpr int NW = NT / 32;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t t0 = a.tstart[b];
-    const int n = (int)(a.tstart[b + 1] - t0);
-    const V span = (V)a.span[b];
-    const double eps_b = tile_eps(a, b);
-    const double inv_eps_b = a.teps ? 1.0 / eps_b : a.inv_eps;
-    load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
-
-    // ranks of the target points (forward order)
-    {
-        int cntt = 0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const int r = tid * C + c;
-            if (r < n && sm.mid[r] == a.j) ++cntt;
-        }
-        int incl = cntt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) sm.ired[w] = incl;
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int q = 0; q < NW; ++q) {
-                const int t = sm.ired[q];
-                sm.ired[q] = acc;
-                acc += t;
-            }
-            sm.ntarget = acc;
-        }
-        __syncthreads();
-        int rank = sm.ired[w] + incl - cntt;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const int r = tid * C + c;
-            if (r < n && sm.mid[r] == a.j) sm.slot[r] = (int16_t)(rank++);
-        }
-        __syncthreads();
-    }
-    if (sm.ntarget > JCAP) {
-        if (tid == 0) atomicOr(a.err, ERR_RANGE);
-    }
-    // prefetch ln mu of the target points (consecutive local indices) into
-    // shared memory; waited for before the epilogue
-    const int32_t off0 = a.cnt[(size_t)b * a.l + a.j];
-    if (a.mode == MODE_UPDATE) {
-        const int nq = min(sm.ntarget, JCAP);
-        for (int q = tid; q < nq; q += NT) __pipeline_memcpy_async(&sm.lmu[q], a.lnmuj + off0 + q, sizeof(double));
-    }
-    __pipeline_commit();
-
-    En e;
-    // ---- backward states inside the tile from the stored carry -------------
-    e.setup(sm, n, span, false, a.j);
-    for (int S = tid; S < NS; S += NT) {
-        sm.E[S] = sf_load<V>(sfp<V>(a.bcarry)[(size_t)b * NS + S]);
-        sm.Eh[S] = sf_scale_exp(sm.E[S], -En::sum_beta(sm, S));
-    }
-    __syncthreads();
-    e.template all_levels<false>(sm, a, v, b, false);
-    e.template walk<NB>([&](int c) {
-        const int sl = sm.slot[e.idx[c]];
-        if (sl < JCAP) {
-#pragma unroll
-            for (int U = 0; U < NS; ++U) sm.G[U * JCAP + sl] = (U == 0) ? V(1) : (e.carry[U] + e.run[U]);
-        }
-    });
-    for (int S = tid; S < NS; S += NT) sm.GsG[S] = sm.Gs[S];
-    __syncthreads();
-
-    // ---- forward states (look-back or stored carry), then combine ----------
-    e.setup(sm, n, span, true, a.j);
-    if constexpr (LOOKBACK) {
-        e.template all_levels<true>(sm, a, v, b, true);
-    } else {
-        for (int S = tid; S < NS; S += NT) {
-            sm.E[S] = sf_load<V>(sfp<V>(a.fcarry)[(size_t)b * NS + S]);
-            sm.Eh[S] = sf_scale_exp(sm.E[S], -En::sum_beta(sm, S));
-        }
-        __syncthreads();
-        e.template all_levels<false>(sm, a, v, b, true);
-    }
-
-    // per-tile constants of the combine: binary exponent of the product of the
-    // two states' scales, and the FP64 base
-    __shared__ double s_base;
-    __shared__ int s_emax, s_fast;
-    __shared__ V s_sc[NS];
-    for (int S = tid; S < NS; S += NT) sm.eS[S] = (sm.Gs[S].k - 1) + (sm.GsG[FULLS ^ S].k - 1);
-    __syncthreads();
-    if (tid == 0) {
-        double sb = 0.0;
-        for (int k = 0; k < NB; ++k) sb += sm.beta[k];
-        s_base = sb;
-        int emx = INT_MIN, emn = INT_MAX;
-        for (int S = 0; S < NS; ++S) {
-            emx = max(emx, sm.eS[S]);
-            emn = min(emn, sm.eS[S]);
-        }
-        s_emax = emx;
-        // fast combine when the states' scales lie within 2^60 of each other
-        s_fast = (emx - emn <= 60) ? 1 : 0;
-    }
-    __syncthreads();
-    for (int S = tid; S < NS; S += NT) s_sc[S] = pow2neg<V>(sm.eS[S] - s_emax);
-    __syncthreads();
-    const bool fast = (s_fast != 0);
-    const int emax_t = s_emax;
-    // ln M = base + xE ln 2 + xM: per-tile FP64 base, the binary exponent of
-    // the largest term and a small in-tile part.  Every term F_S G_{R\S} is
-    // formed as mantissa x 2^exponent, so terms whose states carry very
-    // different scales neither overflow nor underflow.
-    V xM[C];
-    int xE[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        xM[c] = V(0);
-        xE[c] = 0;
-    }
-    const double base = s_base;
-    e.template walk<NB>([&](int c) {
-        const int sl = sm.slot[e.idx[c]];
-        const V pF = e.pp[c];
-        const V pG = span - pF;
-        V q[NB + 1];
-#pragma unroll
-        for (int s = 0; s <= NB; ++s) q[s] = vexp<V>(-(En::rate(s) * pF + En::rate(NB - s) * pG));
-        int Emax = INT_MIN / 2;
-        V sum = V(0);
-        if (fast && sl < JCAP) {
-            // plain products relative to the tile's largest state scale: a sum
-            // above 2^-100 means every term that matters was formed exactly
-#pragma unroll(En::UNR)
-            for (int S = 0; S < NS; ++S) {
-                const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
-                sum = fma(fS * sm.G[(FULLS ^ S) * JCAP + sl], s_sc[S] * q[popc_c(S)], sum);
-            }
-            if (sum >= pow2neg<V>(-100)) {
-                Emax = emax_t;
-            } else {
-                sum = V(0);
-            }
-        }
-        if (sum == V(0) && sl < JCAP) {
-#pragma unroll(En::UNR)
-            for (int S = 0; S < NS; ++S) {
-                const V fS = (S == 0) ? V(1) : (e.carry[S] + e.run[S]);
-                const Sf<V> fm = sf_make<V>(fS);
-                const Sf<V> gm = sf_make<V>(sm.G[(FULLS ^ S) * JCAP + sl]);
-                if (fm.m != V(0) && gm.m != V(0)) {
-                    const V z = fm.m * gm.m * q[popc_c(S)];
-                    const int E = fm.k + gm.k + sm.eS[S];
-                    if (E > Emax) {
-                        sum = fma(sum, pow2neg<V>(Emax - E), z);
-                        Emax = E;
-                    } else {
-                        sum = fma(z, pow2neg<V>(E - Emax), sum);
-                    }
-                }
-            }
-        }
-        xM[c] = (sum > V(0)) ? vlog<V>(sum) : V(-INFINITY);
-        xE[c] = (sum > V(0)) ? Emax : 0;
-    });
-
-    // ---- FP64 epilogue ------------------------------------------------------
-    const int32_t off = off0;
-    __pipeline_wait_prior(0);
-    __syncthreads();   // the combine no longer reads sm.G
-    if constexpr (NB >= 2) {
-        // by target slot instead of by chunk position: the FP64 work of a
-        // target runs once, not once per chunk step of a warp whose lanes hold
-        // targets at different steps.  Per slot xM, xE and g/eps live in the
-        // space of the backward states.
-        using SmT = SweepSmem<NB, V, NT, C, JCAP, true>;
-        static_assert(offsetof(SmT, G) % 16 == 0 &&
-                          ((size_t)JCAP * (sizeof(V) + sizeof(int))) % alignof(double) == 0,
-                      "epilogue scratch alignment");
-        unsigned char *rb = reinterpret_cast<unsigned char *>(sm.G);
-        V *bxm = reinterpret_cast<V *>(rb);
-        int *bxe = reinterpret_cast<int *>(rb + (size_t)JCAP * sizeof(V));
-        double *bgq = reinterpret_cast<double *>(rb + (size_t)JCAP * (sizeof(V) + sizeof(int)));
-        static_assert((size_t)JCAP * (sizeof(V) + sizeof(int) + sizeof(double)) <= sizeof(V) * SweepSmem<NB, V, NT, C, JCAP, true>::GSZ,
-                      "epilogue scratch");
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            if (e.bit[c] == -1) {
-                const int sl = sm.slot[e.idx[c]];
-                if (sl < JCAP) {
-                    bxm[sl] = xM[c];
-                    bxe[sl] = xE[c];
-                }
-            }
-        }
-        __syncthreads();
-        const int ntg = min(sm.ntarget, JCAP);
-        if (a.mode == MODE_UPDATE) {
-            // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base - xE ln 2) - xM   (FP64)
-            V qmax = V(-INFINITY);   // new baseline: the tile maximum of g_j/eps
-            bool bad = false;
-            for (int sl = tid; sl < ntg; sl += NT) {
-                const double lm = sm.lmu[sl];
-                double g = -INFINITY;
-                if (lm > -INFINITY) {
-                    g = (lm - base - (double)bxe[sl] * kLn2) - (double)bxm[sl];
-                    if (!isfinite(g)) bad = true;
-                    qmax = fmax(qmax, (V)g);
-                }
-                bgq[sl] = g;
-                a.gj[off + sl] = eps_b * g;
-            }
-            if (bad) atomicOr(a.err, ERR_NONFINITE);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
-            if (lane == 0) sm.fred[w][0] = qmax;
-            __syncthreads();
-            if (tid == 0) {
-                V x = V(-INFINITY);
-                for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][0]);
-                const double bx = isfinite((double)x) ? (double)x : 0.0;
-                sm.dred[0] = bx;
-                if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = bx;
-            }
-            __syncthreads();
-            const double bnew = sm.dred[0];
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                if (e.bit[c] == -1) {
-                    const V lp = (V)(bgq[sm.slot[e.idx[c]]] - bnew);
-                    static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
-                    sm.lphi[e.idx[c]] = lp;
-                }
-            }
-        } else if (a.mode == MODE_RESIDUAL) {
-            double acc = 0.0;
-            for (int sl = tid; sl < ntg; sl += NT) {
-                const int i = off + sl;
-                const double gg = a.gj[i];
-                const double marg = (gg == -INFINITY || bxm[sl] == V(-INFINITY))
-                                        ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)bxe[sl] * kLn2 + (double)bxm[sl]));
-                acc += fabs(marg - a.muj[i]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-            if (lane == 0) sm.dred[w] = acc;
-            __syncthreads();
-            if (tid == 0) {
-                double x = 0.0;
-                for (int q = 0; q < NW; ++q) x += sm.dred[q];
-                a.partial[b] = x;
-            }
-        } else {
-            for (int sl = tid; sl < ntg; sl += NT) {
-                const int i = off + sl;
-                const double lnMc = (bxm[sl] == V(-INFINITY)) ? -INFINITY : base + (double)bxe[sl] * kLn2 + (double)bxm[sl];
-                double r;
-                if (a.mode == MODE_OUT_M)
-                    r = exp_acc<V>(lnMc);
-                else if (a.mode == MODE_OUT_PLAN)
-                    r = (a.gj[i] == -INFINITY) ? 0.0 : exp_acc<V>(a.gj[i] * inv_eps_b + lnMc);
-                else
-                    r = lnMc;
-                a.out[i] = r;
-            }
-        }
-    } else {
-        if (a.mode == MODE_UPDATE) {
-            // g_j/eps = ln mu_j - ln M_j = (ln mu_j - base) - xM   (FP64)
-            double gq[C];
-            V qmax = V(-INFINITY);   // new baseline: the tile maximum of g_j/eps
-            bool bad = false;
-    #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                gq[c] = -INFINITY;
-                if (e.bit[c] == -1) {
-                    const double lm = sm.lmu[sm.slot[e.idx[c]]];
-                    if (lm > -INFINITY) {
-                        gq[c] = (lm - base - (double)xE[c] * kLn2) - (double)xM[c];
-                        if (!isfinite(gq[c])) bad = true;
-                        qmax = fmax(qmax, (V)gq[c]);
-                    }
-                }
-            }
-            if (bad) atomicOr(a.err, ERR_NONFINITE);
-    #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
-            if (lane == 0) sm.fred[w][0] = qmax;
-            __syncthreads();
-            if (tid == 0) {
-                V x = V(-INFINITY);
-                for (int q = 0; q < NW; ++q) x = fmax(x, sm.fred[q][0]);
-                const double bx = isfinite((double)x) ? (double)x : 0.0;
-                sm.dred[0] = bx;
-                if (sm.ntarget > 0) a.beta[(size_t)b * a.l + a.j] = bx;
-            }
-            __syncthreads();
-            const double bnew = sm.dred[0];
-    #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                if (e.bit[c] == -1) {
-                    const int i = off + sm.slot[e.idx[c]];
-                    a.gj[i] = eps_b * gq[c];
-                    const V lp = (V)(gq[c] - bnew);
-                    static_cast<V *>(a.lphi)[t0 + e.idx[c]] = lp;
-                    sm.lphi[e.idx[c]] = lp;
-                }
-            }
-        } else if (a.mode == MODE_RESIDUAL) {
-            double acc = 0.0;
-    #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                if (e.bit[c] == -1) {
-                    const int i = off + sm.slot[e.idx[c]];
-                    const double gg = a.gj[i];
-                    const double marg = (gg == -INFINITY || xM[c] == V(-INFINITY))
-                                            ? 0.0 : exp_acc<V>(gg * inv_eps_b + (base + (double)xE[c] * kLn2 + (double)xM[c]));
-                    acc += fabs(marg - a.muj[i]);
-                }
-            }
-    #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-            if (lane == 0) sm.dred[w] = acc;
-            __syncthreads();
-            if (tid == 0) {
-                double x = 0.0;
-                for (int q = 0; q < NW; ++q) x += sm.dred[q];
-                a.partial[b] = x;
-            }
-        } else {
-    #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                if (e.bit[c] == -1) {
-                    const int i = off + sm.slot[e.idx[c]];
-                    const double lnMc = (xM[c] == V(-INFINITY)) ? -INFINITY : base + (double)xE[c] * kLn2 + (double)xM[c];
-                    double r;
-                    if (a.mode == MODE_OUT_M)
-                        r = exp_acc<V>(lnMc);
-                    else if (a.mode == MODE_OUT_PLAN)
-                        r = (a.gj[i] == -INFINITY) ? 0.0 : exp_acc<V>(a.gj[i] * inv_eps_b + lnMc);
-                    else
-                        r = lnMc;
-                    a.out[i] = r;
-                }
-            }
-        }
-    }
-    __syncthreads();
-}
-
 // Carry-free transfer operator of tile b for target j in one direction,
 // stored as scaled floats with the decay to the next tile base (processing
 // order) included:
@@ -1432,28 +1066,6 @@ __global__ void __launch_bounds__(NT, 3) k_tileop(SweepArgs a)
     load_tile<NB, V, NT, C, JCAP, true>(sm, a, b, n, t0, a.j);
     tile_operator<NB, V, NT, C, JCAP, L>(sm, a, b, n, a.j, true);
     tile_operator<NB, V, NT, C, JCAP, L>(sm, a, b, n, a.j, false);
-}
-
-template <int NB, typename V, int NT, int C, int JCAP>
-__global__ void __launch_bounds__(NT, 3) k_prod(SweepArgs a)
-{
-    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Sm &sm = *reinterpret_cast<Sm *>(smraw);
-    const int b = blockIdx.x;
-    if (skip_tile(a, b)) return;
-    product_body<NB, V, NT, C, JCAP, false>(sm, a, b, b);
-    if constexpr (NB <= kMaxOpBits) {
-        if (a.jnext >= 0) {
-            // operators of the next target from the updated potentials of this tile
-            const uint32_t t0 = a.tstart[b];
-            const int n = (int)(a.tstart[b + 1] - t0);
-            load_betas(sm, a, b, a.jnext);
-            __syncthreads();
-            tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, true);
-            tile_operator<NB, V, NT, C, JCAP>(sm, a, b, n, a.jnext, false);
-        }
-    }
 }
 
 // ---- level passes (many state bits) -----------------------------------------
@@ -1871,18 +1483,6 @@ cudaError_t launch_tileop_impl(const SweepArgs &a, cudaStream_t st)
 {
     using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
     auto kern = k_tileop<NB, V, NT, C, JCAP, L>;
-    const size_t sz = sizeof(Sm);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
-    if (e != cudaSuccess) return e;
-    kern<<<a.nt, NT, sz, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int NB, typename V, int NT, int C, int JCAP>
-cudaError_t launch_prod_impl(const SweepArgs &a, cudaStream_t st)
-{
-    using Sm = SweepSmem<NB, V, NT, C, JCAP, true>;
-    auto kern = k_prod<NB, V, NT, C, JCAP>;
     const size_t sz = sizeof(Sm);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
     if (e != cudaSuccess) return e;

@@ -11,14 +11,12 @@
     template <>                                                                        \
     cudaError_t launch_tileop<NB_, V_>(const SweepArgs &a, cudaStream_t s)             \
     {                                                                                  \
-        using S = Shape<NB_, V_>;                                                      \
-        return launch_tops_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                  \
+        return launch_tops_impl<NB_, V_>(a, s);                                        \
     }                                                                                  \
     template <>                                                                        \
     cudaError_t launch_prod<NB_, V_>(const SweepArgs &a, cudaStream_t s)               \
     {                                                                                  \
-        using S = Shape<NB_, V_>;                                                      \
-        return launch_tile_impl<NB_, V_, S::NT, S::C, S::JCAP>(a, s);                  \
+        return launch_tile_impl<NB_, V_>(a, s);                                        \
     }                                                                                  \
     template <>                                                                        \
     cudaError_t launch_carry<NB_, V_>(const SweepArgs &a, cudaStream_t s)              \

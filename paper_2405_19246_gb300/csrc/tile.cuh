@@ -44,6 +44,7 @@
 // (one walk computing the forward and the backward operator, composed over
 // the lanes and warps), stored for the next carry scan.
 #pragma once
+
 #include "shapes.cuh"
 #include "sweep.cuh"
 
@@ -120,12 +121,29 @@ __host__ __device__ constexpr bool op_ok(int s, int V)
     return V != 0 && s < NB && s + popc_c(V) <= NB;
 }
 
-// Forward operator, one point of bit k (runtime) appended on the right:
-//   F[s][V] += [k in V] fac[s + |V|] F[s][V \ k]   (F[s][0] = 1).
-// k < 0 (target, padding) leaves F unchanged.  Branch-free: the lanes of a
-// warp hold points of different marginals.
+// One-hot factors of a point: fe[s][k] = fac[s] if the point's bit is k,
+// else 0 (k < 0: target or padding, all 0).  The injections below then need
+// no per-lane selection of their source: the lanes of a warp hold points of
+// different marginals, and every term is an FMA with a zero factor except
+// the one of the point's marginal.
 template <int NB, typename V>
-__device__ __forceinline__ void op_push_right(V (&op)[NB][1 << NB], int k, const V (&fac)[NB + 1])
+__device__ __forceinline__ void onehot(int k, const V (&fac)[NB + 1], V (&fe)[NB + 1][NB])
+{
+    static_for<1, NB + 1>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<0, NB>([&](auto kc) {
+            constexpr int kb = decltype(kc)::value;
+            fe[s][kb] = (k == kb) ? fac[s] : V(0);
+        });
+    });
+}
+
+// Forward operator, one point appended on the right:
+//   F[s][V] += fac[s + |V|] F[s][V \ k]  for the point's bit k in V (F[s][0] = 1).
+// (A term of another bit has a zero factor, so the order of the in-place
+// updates does not matter.)
+template <int NB, typename V>
+__device__ __forceinline__ void op_push_right(V (&op)[NB][1 << NB], const V (&fe)[NB + 1][NB])
 {
     constexpr int NS = 1 << NB;
     static_for<0, NB>([&](auto sc) {
@@ -133,18 +151,18 @@ __device__ __forceinline__ void op_push_right(V (&op)[NB][1 << NB], int k, const
         static_for<1, NS>([&](auto vc) {
             constexpr int Vv = decltype(vc)::value;
             if constexpr (op_ok<NB>(s, Vv)) {
-                V src = V(0);
+                V acc = op[s][Vv];
                 static_for<0, NB>([&](auto kc) {
                     constexpr int kb = decltype(kc)::value;
                     if constexpr ((Vv >> kb) & 1) {
                         constexpr int W = Vv ^ (1 << kb);
                         if constexpr (W == 0)
-                            src = (k == kb) ? V(1) : src;
+                            acc += fe[s + 1][kb];
                         else
-                            src = (k == kb) ? op[s][W] : src;
+                            acc = fma(fe[s + popc_c(Vv)][kb], op[s][W], acc);
                     }
                 });
-                op[s][Vv] = fma(fac[s + popc_c(Vv)], src, op[s][Vv]);
+                op[s][Vv] = acc;
             }
         });
     });
@@ -152,9 +170,9 @@ __device__ __forceinline__ void op_push_right(V (&op)[NB][1 << NB], int k, const
 
 // Backward operator built in forward point order: the new point is the first
 // one the backward pass meets, so it is composed on the left:
-//   B[s][V] += [k in V] fac[s + 1] B[s + 1][V \ k]   (B[.][0] = 1).
+//   B[s][V] += fac[s + 1] B[s + 1][V \ k]   (B[.][0] = 1).
 template <int NB, typename V>
-__device__ __forceinline__ void op_push_left(V (&op)[NB][1 << NB], int k, const V (&fac)[NB + 1])
+__device__ __forceinline__ void op_push_left(V (&op)[NB][1 << NB], const V (&fe)[NB + 1][NB])
 {
     constexpr int NS = 1 << NB;
     static_for<0, NB>([&](auto sc) {
@@ -162,18 +180,18 @@ __device__ __forceinline__ void op_push_left(V (&op)[NB][1 << NB], int k, const 
         static_for<1, NS>([&](auto vc) {
             constexpr int Vv = decltype(vc)::value;
             if constexpr (op_ok<NB>(s, Vv)) {
-                V src = V(0);
+                V acc = op[s][Vv];
                 static_for<0, NB>([&](auto kc) {
                     constexpr int kb = decltype(kc)::value;
                     if constexpr ((Vv >> kb) & 1) {
                         constexpr int W = Vv ^ (1 << kb);
                         if constexpr (W == 0)
-                            src = (k == kb) ? V(1) : src;
+                            acc += fe[s + 1][kb];
                         else
-                            src = (k == kb) ? op[s + 1][W] : src;
+                            acc = fma(fe[s + 1][kb], op[s + 1][W], acc);
                     }
                 });
-                op[s][Vv] = fma(fac[s + 1], src, op[s][Vv]);
+                op[s][Vv] = acc;
             }
         });
     });
@@ -209,63 +227,6 @@ __device__ __forceinline__ void op_zero(V (&op)[NB][1 << NB])
         for (int U = 0; U < (1 << NB); ++U) op[s][U] = V(0);
 }
 
-template <int NB, typename V>
-__device__ __forceinline__ void op_shfl_xor(const V (&X)[NB][1 << NB], V (&Y)[NB][1 << NB], int o)
-{
-    static_for<0, NB>([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        static_for<1, (1 << NB)>([&](auto vc) {
-            constexpr int Vv = decltype(vc)::value;
-            if constexpr (op_ok<NB>(s, Vv)) Y[s][Vv] = __shfl_xor_sync(0xffffffffu, X[s][Vv], o);
-        });
-    });
-}
-
-// Butterfly over the lanes of a warp: every lane ends with the composition of
-// the warp's operators in lane order (fwd: lane 0 first; otherwise lane 31
-// first, the order of the backward pass).  At each step the pair's operators
-// X (this lane's) and Y (the partner's) are composed with the lower-ordered
-// one first; the operand selection is folded into the terms.
-template <int NB, typename V>
-__device__ __forceinline__ void op_warp_reduce(V (&op)[NB][1 << NB], bool lane_order)
-{
-    constexpr int NS = 1 << NB;
-    const int lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int o = 1; o < 32; o <<= 1) {
-        V Y[NB][NS];
-        op_shfl_xor<NB, V>(op, Y, o);
-        const bool first = (((lane & o) == 0) == lane_order);   // this lane's operator is applied first
-        V R[NB][NS];
-        static_for<0, NB>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<1, NS>([&](auto vc) {
-                constexpr int Vv = decltype(vc)::value;
-                if constexpr (op_ok<NB>(s, Vv)) {
-                    V r = op[s][Vv] + Y[s][Vv];
-                    static_for<1, NS>([&](auto wc) {
-                        constexpr int W1 = decltype(wc)::value;
-                        if constexpr ((W1 & ~Vv) == 0 && W1 != Vv) {
-                            constexpr int s2 = s + popc_c(W1);
-                            const V a1 = first ? op[s][W1] : Y[s][W1];
-                            const V b1 = first ? Y[s2][Vv ^ W1] : op[s2][Vv ^ W1];
-                            r = fma(a1, b1, r);
-                        }
-                    });
-                    R[s][Vv] = r;
-                }
-            });
-        });
-        static_for<0, NB>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<1, NS>([&](auto vc) {
-                constexpr int Vv = decltype(vc)::value;
-                if constexpr (op_ok<NB>(s, Vv)) op[s][Vv] = R[s][Vv];
-            });
-        });
-    }
-}
-
 // number of valid operator entries
 template <int NB>
 __host__ __device__ constexpr int op_count()
@@ -277,7 +238,28 @@ __host__ __device__ constexpr int op_count()
     return c;
 }
 
-template <int NB, typename V, int NT, int JCAP>
+// index of entry (s, U) among the valid entries (s-major, then U)
+template <int NB>
+__host__ __device__ constexpr int op_index(int s, int U)
+{
+    int c = 0;
+    for (int s2 = 0; s2 < NB; ++s2)
+        for (int U2 = 1; U2 < (1 << NB); ++U2)
+            if (op_ok<NB>(s2, U2)) {
+                if (s2 == s && U2 == U) return c;
+                ++c;
+            }
+    return -1;
+}
+
+// resident blocks per SM the register allocation is sized for (FP32: three
+// 128-thread or two 256-thread tiles; FP64: the registers it needs)
+template <typename V, int NT>
+struct TileMinBlocks {
+    static constexpr int value = (sizeof(V) == 4) ? (NT >= 256 ? 2 : 3) : 1;
+};
+
+template <int NB, typename V, int NT, int C, int JCAP>
 struct TileSm {
     static constexpr int NS = 1 << NB;
     static constexpr int NW = NT / 32;
@@ -294,19 +276,24 @@ struct TileSm {
     int emax;             // combine: largest term exponent
     int fast;             // combine: every term within 2^60 of the largest
     // per target slot: ln M as mantissa (lmx) and binary exponent (lme) after
-    // the combine; the new scaled phi and ln phi after the update
+    // the combine; the new scaled phi and ln phi after the update; e^{pos}
     alignas(16) V lmx[JCAP];
     int lme[JCAP];
-    // backward states at the target slots (state U at row U - 1); after the
-    // combine, the warps' transfer operators
-    static constexpr int GSZ = (NS - 1) * JCAP;
-    static constexpr int OSZ = NW * 2 * NB * NS;
-    alignas(16) V buf[GSZ > OSZ ? GSZ : OSZ];
-    // forward states (state S at row S - 1) and e^{pos} at the target slots:
-    // the combine runs by slot after the forward walk, so a warp does not
-    // run it at every chunk position where one of its lanes has a target
-    alignas(16) V fst[(NS - 1) * JCAP];
     V tpe[JCAP];
+    // backward states (state U at row U - 1) then forward states at the
+    // target slots; afterwards the lanes' transfer operators of the next
+    // target ([dir][entry][lane])
+    static constexpr int GSZ = (NS - 1) * JCAP;
+    static constexpr int OSZ = 2 * NOP * NT;
+    alignas(16) V area[2 * GSZ > OSZ ? 2 * GSZ : OSZ];
+    // the lanes' points, [c][lane] (each lane reads only its own points, in
+    // rolled loops: registers would need fully unrolled walks, whose code
+    // does not fit the instruction cache)
+    alignas(16) V pph[C * NT];   // scaled phi
+    V ppe[C * NT];               // e^{pos}
+    uint8_t pmd[C * NT];         // marginal (0xff: padding)
+    __device__ V *gst() { return area; }
+    __device__ V *fst() { return area + GSZ; }
 };
 
 // Per-tile constants of one pass, identical in every lane.
@@ -316,97 +303,83 @@ struct PassC {
     int e[1 << NB];    // final binary scale of every state (e[0] = 0)
 };
 
-template <int NB, typename V, int NT, int C, int JCAP, bool WITH_NEXT>
+template <int NB, typename V, int NT, int C, int JCAP>
 struct TileRun {
     static constexpr int NS = 1 << NB;
     static constexpr int NW = NT / 32;
     static constexpr int L = NB + 1;
     static constexpr int K = NT * C;
     static constexpr unsigned FULL = 0xffffffffu;
-    using Sm = TileSm<NB, V, NT, JCAP>;
+    using Sm = TileSm<NB, V, NT, C, JCAP>;
 
     int lane, w, tid;
     int n;            // points in the tile
+    int jcur;         // target whose bit mapping bt() uses
     V span;
-    V ph[C], pe[C], pm[C];
-    unsigned mdw[(C + 3) / 4];   // marginal of each point, 4 per word (0xff: padding)
-    int bt[C];        // bit of the point for the current target (-1 target, -2 none)
+    Sm *sp;           // the block's shared memory (per-point arrays)
 
     __device__ static constexpr int rate(int s) { return s * (L - s); }
+    __device__ static constexpr int arate(int s) { return rate(s) - rate(s - 1); }   // L + 1 - 2s
 
-    // the lane's C points: e^{pos}, e^{-pos}, scaled phi and marginal, and the
-    // bit of each point for target j
-    __device__ __forceinline__ void load(const SweepArgs &a, int b, uint32_t t0, int i0, int j)
+    __device__ __forceinline__ V ph(int c) const { return sp->pph[c * NT + tid]; }
+    __device__ __forceinline__ V pe(int c) const { return sp->ppe[c * NT + tid]; }
+    __device__ __forceinline__ void set_ph(int c, V v) { sp->pph[c * NT + tid] = v; }
+    __device__ __forceinline__ int mid_of(int c) const { return sp->pmd[c * NT + tid]; }
+    __device__ __forceinline__ static int bit_of(int m, int j) { return (m == 0xff) ? -2 : (m == j ? -1 : (m < j ? m : m - 1)); }
+    // bit of point c for the current target: 0..NB-1, -1 target, -2 padding
+    __device__ __forceinline__ int bt(int c) const { return bit_of(mid_of(c), jcur); }
+    __device__ __forceinline__ void set_bits(int j) { jcur = j; }
+
+    // the lane's C points (e^{pos}, scaled phi, marginal) into shared memory
+    __device__ __forceinline__ void load(const SweepArgs &a, uint32_t t0, int i0)
     {
         const V *epos = static_cast<const V *>(a.epos);
         const V *ephi = static_cast<const V *>(a.ephi);
+        constexpr int PV = 16 / sizeof(V);   // values per 16-byte load
+        static_assert(C % PV == 0 && C % 4 == 0, "chunk of whole 16-byte pieces");
         if (i0 < n) {
-            constexpr int PV = 16 / sizeof(V);   // values per 16-byte load
-            static_assert(C % PV == 0 || C < PV, "chunk of whole 16-byte pieces");
-            if constexpr (C >= PV) {
 #pragma unroll
-                for (int q = 0; q < C / PV; ++q) {
-                    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(epos + t0 + i0) + q);
-                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ephi + t0 + i0) + q);
-                    memcpy(&pe[q * PV], &u, 16);
-                    memcpy(&ph[q * PV], &v, 16);
-                }
-            } else {
+            for (int q = 0; q < C / PV; ++q) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4 *>(epos + t0 + i0) + q);
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ephi + t0 + i0) + q);
+                V pu[PV], pv[PV];
+                memcpy(pu, &u, 16);
+                memcpy(pv, &v, 16);
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    pe[c] = epos[t0 + i0 + c];
-                    ph[c] = ephi[t0 + i0 + c];
+                for (int e = 0; e < PV; ++e) {
+                    sp->ppe[(q * PV + e) * NT + tid] = pu[e];
+                    sp->pph[(q * PV + e) * NT + tid] = pv[e];
                 }
             }
-            if constexpr (C == 16) {
-                const uint4 u = __ldg(reinterpret_cast<const uint4 *>(a.emid + t0 + i0));
-                mdw[0] = u.x;
-                mdw[1] = u.y;
-                mdw[2] = u.z;
-                mdw[3] = u.w;
-            } else if constexpr (C == 8) {
-                const uint2 u = __ldg(reinterpret_cast<const uint2 *>(a.emid + t0 + i0));
-                mdw[0] = u.x;
-                mdw[1] = u.y;
-            } else if constexpr (C == 4) {
-                mdw[0] = __ldg(reinterpret_cast<const unsigned *>(a.emid + t0 + i0));
-            } else {
-                unsigned w0 = 0xffffffffu;
 #pragma unroll
-                for (int c = 0; c < C; ++c) w0 = (w0 & ~(0xffu << (8 * c))) | ((unsigned)a.emid[t0 + i0 + c] << (8 * c));
-                mdw[0] = w0;
+            for (int q = 0; q < C / 4; ++q) {
+                const unsigned u = __ldg(reinterpret_cast<const unsigned *>(a.emid + t0 + i0) + q);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) sp->pmd[(q * 4 + e) * NT + tid] = (uint8_t)(u >> (8 * e));
             }
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                pe[c] = V(1);
-                ph[c] = V(0);
+                sp->ppe[c * NT + tid] = V(1);
+                sp->pph[c * NT + tid] = V(0);
+                sp->pmd[c * NT + tid] = 0xff;
             }
-#pragma unroll
-            for (int q = 0; q < (C + 3) / 4; ++q) mdw[q] = 0xffffffffu;
-        }
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            pm[c] = V(1) / pe[c];
-            bt[c] = bit_of(mid_of(c), j);
         }
     }
 
-    __device__ __forceinline__ int mid_of(int c) const { return (mdw[c >> 2] >> (8 * (c & 3))) & 0xff; }
-
-    __device__ __forceinline__ static int bit_of(int m, int j) { return (m == 0xff) ? -2 : (m == j ? -1 : (m < j ? m : m - 1)); }
-    __device__ static constexpr int arate(int s) { return rate(s) - rate(s - 1); }   // L + 1 - 2s
-
-    // e^{a p} for the point in the pass frame: forward p = pos (pe^a),
-    // backward p = span - pos (e^{a span} pm^a; the e^{a span} is in cf)
+    // injection factors of point c in the pass frame, levels 1..NB:
+    // forward p = pos (pe^a), backward p = span - pos (e^{a span} pe^{-a};
+    // the e^{a span} is in cf)
     template <bool FWD>
     __device__ __forceinline__ void facs(int c, const PassC<NB, V> &P, V (&f)[NB + 1]) const
     {
-        const V up = FWD ? pe[c] : pm[c];
-        const V dn = FWD ? pm[c] : pe[c];
-        // a_s = L + 1 - 2 s = NB + 2 - 2 s: NB, NB - 2, ..., 2 - NB
+        const V pc = pe(c);
+        const V pinv = V(1) / pc;
+        const V up = FWD ? pc : pinv;
+        const V dn = FWD ? pinv : pc;
         const V up2 = up * up, dn2 = dn * dn;
-        V pw[NB + 1];
+        const V phc = ph(c);
+        f[0] = V(0);
         static_for<1, NB + 1>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
             constexpr int a = arate(s);
@@ -420,12 +393,7 @@ struct TileRun {
             else if constexpr (a == -2) x = dn2;
             else if constexpr (a == -3) x = dn2 * dn;
             else x = dn2 * dn2;
-            pw[s] = x;
-        });
-        f[0] = V(0);
-        static_for<1, NB + 1>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            f[s] = (ph[c] * P.cf[s]) * pw[s];
+            f[s] = (phc * P.cf[s]) * x;
         });
     }
 
@@ -441,9 +409,6 @@ struct TileRun {
         for (int S = 0; S < NS; ++S) P.e[S] = 0;
     }
 
-    // Steps 1-2 of a pass: chunk-start values x[] (final per-state scales in
-    // P.e) from the tile carries.  cu: on lane T < NS, the carry of state T in
-    // the unscaled tile frame (carry e^{-(sum beta_T + Gamma_|T|)}).
     // Provisional scale of state T: the largest final scale among the lower
     // states U that can reach T inside this tile (every marginal of T \ U
     // has points in the tile: bits), plus headroom for the in-tile sums.  A
@@ -458,6 +423,9 @@ struct TileRun {
         return (m == INT_MIN) ? 0 : m + 32;
     }
 
+    // Steps 1-2 of a pass: chunk-start values x[] (final per-state scales in
+    // P.e) from the tile carries.  cu: on lane T < NS, the carry of state T in
+    // the unscaled tile frame (carry e^{-(sum beta_T + Gamma_|T|)}).
     template <bool FWD>
     __device__ __forceinline__ void chunk_starts(Sm &sm, PassC<NB, V> &P, const Sf<V> cu, V (&x)[NS], int bits)
     {
@@ -465,19 +433,18 @@ struct TileRun {
         // 1. chunk operator
         V op[NB][NS];
         op_zero<NB, V>(op);
-#pragma unroll
+#pragma unroll 4
         for (int i = 0; i < C; ++i) {
             const int c = FWD ? i : C - 1 - i;
-            V f[NB + 1];
+            V f[NB + 1], fe[NB + 1][NB];
             facs<FWD>(c, P, f);
-            op_push_right<NB, V>(op, bt[c], f);
+            onehot<NB, V>(bt(c), f, fe);
+            op_push_right<NB, V>(op, fe);
         }
         x[0] = V(1);
         // 2. level by level
         static_for<1, NB + 1>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            // provisional scale of each state of the level: the largest final
-            // scale of its lower states plus headroom for the in-tile sums
             int pi[NS];
             V loc[NS];
             static_for<1, NS>([&](auto tc) {
@@ -494,7 +461,9 @@ struct TileRun {
                 }
             });
             // warp scan (inclusive, in pass order: ascending lanes forward,
-            // descending backward) and warp totals
+            // descending backward), exclusive by a lane shift (not incl - loc:
+            // the difference would lose a small prefix next to a large own
+            // value), warp totals
             V ex[NS];
             static_for<1, NS>([&](auto tc) {
                 constexpr int T = decltype(tc)::value;
@@ -510,9 +479,6 @@ struct TileRun {
                             if (lane + o < 32) incl += y;
                         }
                     }
-                    // exclusive prefix by a shift, not incl - loc: the
-                    // difference would lose a small prefix next to a large
-                    // own value (sparse supports)
                     if constexpr (FWD) {
                         const V y = __shfl_up_sync(FULL, incl, 1);
                         ex[T] = (lane == 0) ? V(0) : y;
@@ -524,105 +490,169 @@ struct TileRun {
                 }
             });
             __syncthreads();
-            // carry of each state of the level in its provisional frame, the
-            // tile-end value and the final scale: lane T computes state T
+            // Lane T (state T of the level): the carry in the provisional
+            // frame, the tile-end value R = carry + tile total, the final scale
+            // 2^{e_T} (e_T = pi_T + exponent of R) and, in the final frame, the
+            // carry's share cpf and the factor 2^{-exponent of R} (as two
+            // powers of two) for the in-tile prefixes.
             int eT = 0;
-            Sf<V> cp = sf_zero<V>();
+            V cpf = V(0), ra = V(0), rb = V(0);
             if (lane < NS && popc_c(lane) == s) {
                 const int T = lane;
                 int piT = 0;
 #pragma unroll
                 for (int T2 = 1; T2 < NS; ++T2)
                     if (T2 == T) piT = prov_scale(T2, P.e, bits);
-                cp = cu;
+                Sf<V> cp = cu;
                 if (cp.m != V(0)) cp.k -= piT;
                 V Z = V(0);
 #pragma unroll
                 for (int q = 0; q < NW; ++q) Z += sm.wsum[q][T];
-                const Sf<V> R = sf_add(cp, sf_make<V>(Z));
-                eT = (R.m == V(0)) ? piT : piT + R.k;
+                const Sf<V> Rv = sf_add(cp, sf_make<V>(Z));
+                if (Rv.m == V(0)) {
+                    eT = piT;
+                } else {
+                    eT = piT + Rv.k;
+                    cpf = sf_value(cp, Rv.k);
+                    const int h = -(Rv.k >> 1);
+                    ra = pow2i<V>(h);
+                    rb = pow2i<V>(-Rv.k - h);
+                }
             }
             static_for<1, NS>([&](auto tc) {
                 constexpr int T = decltype(tc)::value;
                 if constexpr (popc_c(T) == s) {
                     P.e[T] = __shfl_sync(FULL, eT, T);
-                    Sf<V> c;
-                    c.m = __shfl_sync(FULL, cp.m, T);
-                    c.k = __shfl_sync(FULL, cp.k, T);
+                    const V c0 = __shfl_sync(FULL, cpf, T);
+                    const V r1 = __shfl_sync(FULL, ra, T);
+                    const V r2 = __shfl_sync(FULL, rb, T);
                     V wp = V(0);
 #pragma unroll
                     for (int q = 0; q < NW; ++q)
                         if (FWD ? (q < w) : (q > w)) wp += sm.wsum[q][T];
-                    const Sf<V> v = sf_add(c, sf_make<V>(wp + ex[T]));
-                    x[T] = sf_value(v, P.e[T] - pi[T]);
+                    x[T] = fma((wp + ex[T]) * r1, r2, c0);
                 }
             });
         });
     }
-};
 
+    // ratios 2^{e_{T\k} - e_T} of the injections of a pass
+    __device__ __forceinline__ static void ratios(const PassC<NB, V> &P, V (&rr)[NS][NB])
+    {
+        static_for<1, NS>([&](auto tc) {
+            constexpr int T = decltype(tc)::value;
+            static_for<0, NB>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                if constexpr ((T >> k) & 1) rr[T][k] = pow2i<V>(P.e[T ^ (1 << k)] - P.e[T]);
+            });
+        });
+    }
+
+    // state walk step: F_T += phi F_{T\k} for every T containing the point's
+    // bit k, in each state's own scale (one-hot factors, no selection)
+    __device__ __forceinline__ static void inject(V (&f)[NS], const V (&fe)[NB + 1][NB], const V (&rr)[NS][NB])
+    {
+        static_for<1, NS>([&](auto tc) {
+            constexpr int T = decltype(tc)::value;
+            V acc = f[T];
+            static_for<0, NB>([&](auto kc) {
+                constexpr int kb = decltype(kc)::value;
+                if constexpr ((T >> kb) & 1) {
+                    constexpr int W = T ^ (1 << kb);
+                    const V g = fe[popc_c(T)][kb] * rr[T][kb];
+                    if constexpr (W == 0)
+                        acc += g;
+                    else
+                        acc = fma(g, f[W], acc);
+                }
+            });
+            f[T] = acc;
+        });
+    }
+};
 
 // ---- transfer operators of one target ----------------------------------------
 // Forward and backward operators of tile b for target jn from the points in
 // the lanes' registers (one walk; the backward operator is built in forward
-// order by composing on the left), composed over the lanes and warps, turned
-// into absolute scaled floats with the decay to the next tile base (processing
-// order) and stored for the carry scan:
+// order by composing on the left), composed over the lanes by a tree in
+// shared memory, turned into absolute scaled floats with the decay to the next
+// tile base (processing order) and stored for the carry scan:
 //   op[b][s][U] = T_b[s][U] exp(sum_{m in U} beta_m + Gamma_{s+|U|} - Gamma_s - w_{s+|U|} d)
 // (T_b in the unscaled tile frame; d the distance to the next base).
+// Expects the caller to have passed a barrier after the last use of sm.area.
 template <int NB, typename V, int NT, int C, int JCAP>
-__device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP, true> &r, TileSm<NB, V, NT, JCAP> &sm, const SweepArgs &a,
-                              int b, int jn)
+__device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP> &r, TileSm<NB, V, NT, C, JCAP> &sm,
+                                              const SweepArgs &a, int b, int jn)
 {
-    using R = TileRun<NB, V, NT, C, JCAP, true>;
+    using R = TileRun<NB, V, NT, C, JCAP>;
     constexpr int NS = 1 << NB;
-    constexpr int NW = NT / 32;
     constexpr int L = NB + 1;
-    const int lane = r.lane, w = r.w;
+    constexpr int NOP = op_count<NB>();
+    const int tid = r.tid;
     PassC<NB, V> PF, PB;
     r.setup_consts(PF, true);
     r.setup_consts(PB, false);
-    V opf[NB][NS], opb[NB][NS];
-    op_zero<NB, V>(opf);
-    op_zero<NB, V>(opb);
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const int k = R::bit_of(r.mid_of(c), jn);
-        V ff[NB + 1], fb[NB + 1];
-        r.template facs<true>(c, PF, ff);
-        r.template facs<false>(c, PB, fb);
-        op_push_right<NB, V>(opf, k, ff);
-        op_push_left<NB, V>(opb, k, fb);
-    }
-    op_warp_reduce<NB, V>(opf, true);
-    op_warp_reduce<NB, V>(opb, false);
-    V *sc = sm.buf;   // [NW][2][NB][NS]
-    if (lane == 0) {
+    {
+        V opf[NB][NS], opb[NB][NS];
+        op_zero<NB, V>(opf);
+        op_zero<NB, V>(opb);
+#pragma unroll 2
+        for (int c = 0; c < C; ++c) {
+            const int k = R::bit_of(r.mid_of(c), jn);
+            V ff[NB + 1], fb[NB + 1], fe[NB + 1][NB];
+            r.template facs<true>(c, PF, ff);
+            r.template facs<false>(c, PB, fb);
+            onehot<NB, V>(k, ff, fe);
+            op_push_right<NB, V>(opf, fe);
+            onehot<NB, V>(k, fb, fe);
+            op_push_left<NB, V>(opb, fe);
+        }
+        V *sc = sm.area;   // [2][NOP][NT]
         static_for<0, NB>([&](auto scc) {
             constexpr int s = decltype(scc)::value;
             static_for<1, NS>([&](auto vc) {
                 constexpr int U = decltype(vc)::value;
                 if constexpr (op_ok<NB>(s, U)) {
-                    sc[((w * 2 + 0) * NB + s) * NS + U] = opf[s][U];
-                    sc[((w * 2 + 1) * NB + s) * NS + U] = opb[s][U];
+                    constexpr int e = op_index<NB>(s, U);
+                    sc[(0 * NOP + e) * NT + tid] = opf[s][U];
+                    sc[(1 * NOP + e) * NT + tid] = opb[s][U];
                 }
             });
         });
     }
+    // tree over the lanes' operators (positions in point order): forward, the
+    // left one first; backward, the right one first
+#pragma unroll 1
+    for (int st = 1; st < NT; st <<= 1) {
+        __syncthreads();
+        if (tid < NT / st) {
+            const int d = tid & 1, p = tid >> 1;
+            const int i0 = 2 * p * st, i1 = i0 + st;
+            V *sc = sm.area + (size_t)d * NOP * NT;
+            V A[NB][NS], B[NB][NS], Rr[NB][NS];
+            static_for<0, NB>([&](auto scc) {
+                constexpr int s = decltype(scc)::value;
+                static_for<1, NS>([&](auto vc) {
+                    constexpr int U = decltype(vc)::value;
+                    if constexpr (op_ok<NB>(s, U)) {
+                        constexpr int e = op_index<NB>(s, U);
+                        const V x0 = sc[e * NT + i0], x1 = sc[e * NT + i1];
+                        A[s][U] = d ? x1 : x0;
+                        B[s][U] = d ? x0 : x1;
+                    }
+                });
+            });
+            op_compose<NB, V>(A, B, Rr);
+            static_for<0, NB>([&](auto scc) {
+                constexpr int s = decltype(scc)::value;
+                static_for<1, NS>([&](auto vc) {
+                    constexpr int U = decltype(vc)::value;
+                    if constexpr (op_ok<NB>(s, U)) sc[op_index<NB>(s, U) * NT + i0] = Rr[s][U];
+                });
+            });
+        }
+    }
     __syncthreads();
-    if (w != 0) return;
-    static_for<0, NB>([&](auto scc) {
-        constexpr int s = decltype(scc)::value;
-        static_for<1, NS>([&](auto vc) {
-            constexpr int U = decltype(vc)::value;
-            if constexpr (op_ok<NB>(s, U)) {
-                opf[s][U] = (lane < NW) ? sc[((lane * 2 + 0) * NB + s) * NS + U] : V(0);
-                opb[s][U] = (lane < NW) ? sc[((lane * 2 + 1) * NB + s) * NS + U] : V(0);
-            }
-        });
-    });
-    op_warp_reduce<NB, V>(opf, true);
-    op_warp_reduce<NB, V>(opb, false);
     // baselines of target jn's bits (beta of the current target just written
     // by this block is visible after the barrier above)
     const int l = a.l;
@@ -650,30 +680,22 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP, true> 
         dB = a.urb[b] - a.urb[b - 1];
         cutB = a.seg && a.seg[b - 1] != a.seg[b];
     }
-    // entries are spread over the lanes: entry e (both directions, [dir][s][U])
-    // goes to lane e % 32
-    constexpr int NE = 2 * NB * NS;
-    constexpr int PER = (NE + 31) / 32;
-    V val[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) val[q] = V(0);
-    static_for<0, NB>([&](auto scc) {
-        constexpr int s = decltype(scc)::value;
-        static_for<1, NS>([&](auto vc) {
-            constexpr int U = decltype(vc)::value;
-            if constexpr (op_ok<NB>(s, U)) {
-                constexpr int eF = (0 * NB + s) * NS + U, eB = (1 * NB + s) * NS + U;
-                if (lane == eF % 32) val[eF / 32] = opf[s][U];
-                if (lane == eB % 32) val[eB / 32] = opb[s][U];
-            }
+    for (int t = tid; t < 2 * NOP; t += NT) {
+        const int dir = t / NOP, e = t % NOP;
+        int s = 0, U = 0;
+        static_for<0, NB>([&](auto scc) {
+            constexpr int s2 = decltype(scc)::value;
+            static_for<1, NS>([&](auto vc) {
+                constexpr int U2 = decltype(vc)::value;
+                if constexpr (op_ok<NB>(s2, U2)) {
+                    if (e == op_index<NB>(s2, U2)) {
+                        s = s2;
+                        U = U2;
+                    }
+                }
+            });
         });
-    });
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int e = q * 32 + lane;
-        if (e >= NE) continue;
-        const int dir = e / (NB * NS), s = (e / NS) % NB, U = e % NS;
-        if (U == 0 || s + __popc(U) > NB) continue;
+        const V val = sm.area[((size_t)dir * NOP + e) * NT];
         const int su = s + __popc(U);
         double bu = 0.0;
 #pragma unroll
@@ -684,11 +706,11 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP, true> 
         const double wsu = (double)su * (double)(L - su);
         double gsu = 0.0, gs = 0.0;
 #pragma unroll
-        for (int t = 0; t <= NB; ++t) {
-            if (t == su) gsu = Gam[t];
-            if (t == s) gs = Gam[t];
+        for (int q = 0; q <= NB; ++q) {
+            if (q == su) gsu = Gam[q];
+            if (q == s) gs = Gam[q];
         }
-        const Sf<V> o = cut ? sf_zero<V>() : sf_scale_exp(sf_make<V>(val[q]), bu + gsu - gs - wsu * d);
+        const Sf<V> o = cut ? sf_zero<V>() : sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d);
         sfp<V>(dir ? a.opB : a.opF)[((size_t)b * NB + s) * NS + U] = sf_store(o);
     }
 }
@@ -696,11 +718,11 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP, true> 
 // Transfer operators of every tile for target a.j (when the stored ones
 // belong to another target).
 template <int NB, typename V, int NT, int C, int JCAP>
-__global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tops(SweepArgs a)
+__global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tops(SweepArgs a)
 {
-    using R = TileRun<NB, V, NT, C, JCAP, true>;
+    using R = TileRun<NB, V, NT, C, JCAP>;
     extern __shared__ __align__(16) unsigned char tsm_raw[];
-    TileSm<NB, V, NT, JCAP> &sm = *reinterpret_cast<TileSm<NB, V, NT, JCAP> *>(tsm_raw);
+    TileSm<NB, V, NT, C, JCAP> &sm = *reinterpret_cast<TileSm<NB, V, NT, C, JCAP> *>(tsm_raw);
     const int b = blockIdx.x;
     R r;
     r.tid = threadIdx.x;
@@ -708,16 +730,17 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tops(SweepArgs a
     r.w = r.tid >> 5;
     r.n = (int)(a.tstart[b + 1] - a.tstart[b]);
     r.span = (V)a.span[b];
-    r.load(a, b, a.toff[b], r.tid * C, a.j);
+    r.sp = &sm;
+    r.load(a, a.toff[b], r.tid * C);
     tile_ops_body<NB, V, NT, C, JCAP>(r, sm, a, b, a.j);
 }
 
 // ---- the tile product ------------------------------------------------------------
 
 template <int NB, typename V, int NT, int C, int JCAP>
-__global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a)
+__global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepArgs a)
 {
-    using R = TileRun<NB, V, NT, C, JCAP, true>;
+    using R = TileRun<NB, V, NT, C, JCAP>;
     using Sm = typename R::Sm;
     constexpr int NS = 1 << NB;
     constexpr int FULLS = NS - 1;
@@ -740,12 +763,18 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
     const int j = a.j;
     const int l = a.l;
 
-    r.load(a, b, t0, i0, j);
+    r.sp = &sm;
+    r.load(a, t0, i0);
+    r.set_bits(j);
 
     // ---- target slots (rank among the tile's targets, forward order) -------
-    int tcount = 0;
-#pragma unroll
-    for (int c = 0; c < C; ++c) tcount += (r.bt[c] == -1);
+    int tcount = 0, lbits = 0;
+#pragma unroll 4
+    for (int c = 0; c < C; ++c) {
+        const int k = r.bt(c);
+        tcount += (k == -1);
+        if (k >= 0) lbits |= 1 << k;
+    }
     int tincl = tcount;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -753,10 +782,6 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
         if (lane >= o) tincl += y;
     }
     if (lane == 31) sm.wcnt[w] = tincl;
-    int lbits = 0;
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-        if (r.bt[c] >= 0) lbits |= 1 << r.bt[c];
     lbits = __reduce_or_sync(FULL, lbits);
     if (lane == 0) sm.wbits[w] = lbits;
     // per-tile FP64 constants: baselines of the marginals mapped to bits
@@ -819,53 +844,35 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
         r.template chunk_starts<false>(sm, PB, cu, x, bits);
     }
     {
-        // ratios 2^{e_{T\k} - e_T} of the injections
         V rr[NS][NB];
-        static_for<1, NS>([&](auto tc) {
-            constexpr int T = decltype(tc)::value;
-            static_for<0, NB>([&](auto kc) {
-                constexpr int k = decltype(kc)::value;
-                if constexpr ((T >> k) & 1) rr[T][k] = pow2i<V>(PB.e[T ^ (1 << k)] - PB.e[T]);
-            });
-        });
+        R::ratios(PB, rr);
         V f[NS];
 #pragma unroll
         for (int S = 0; S < NS; ++S) f[S] = x[S];
         int slot = slot0 + tcount - 1;
-#pragma unroll
+        V *G = sm.gst();
+#pragma unroll 4
         for (int i = 0; i < C; ++i) {
             const int c = C - 1 - i;
-            const int k = r.bt[c];
+            const int k = r.bt(c);
             if (k == -1) {
                 if (slot < JCAP) {
 #pragma unroll
-                    for (int U = 1; U < NS; ++U) sm.buf[(U - 1) * JCAP + slot] = f[U];
+                    for (int U = 1; U < NS; ++U) G[(U - 1) * JCAP + slot] = f[U];
                 }
                 --slot;
             }
-            V fc[NB + 1];
+            V fc[NB + 1], fe[NB + 1][NB];
             r.template facs<false>(c, PB, fc);
-            static_for<1, NS>([&](auto tc) {
-                constexpr int T = decltype(tc)::value;
-                V src = V(0), rat = V(0);
-                static_for<0, NB>([&](auto kc) {
-                    constexpr int kb = decltype(kc)::value;
-                    if constexpr ((T >> kb) & 1) {
-                        src = (k == kb) ? f[T ^ (1 << kb)] : src;
-                        rat = (k == kb) ? rr[T][kb] : rat;
-                    }
-                });
-                f[T] = fma(fc[popc_c(T)] * rat, src, f[T]);
-            });
+            onehot<NB, V>(k, fc, fe);
+            R::inject(f, fe, rr);
         }
 #pragma unroll
         for (int S = 0; S < NS; ++S)
             if (tid == S) sm.eB[S] = PB.e[S];   // (a runtime index would put PB in local memory)
     }
-    // (the chunk_starts barriers of the forward pass order these writes
-    // before the combine reads them)
 
-    // ---- forward pass and combine ------------------------------------------------
+    // ---- forward pass --------------------------------------------------------
     PassC<NB, V> PF;
     r.setup_consts(PF, true);
     {
@@ -879,8 +886,7 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
     // Per term S: F_S G_{R\S} = f g 2^{eF_S + eB_{R\S}} e^{sum beta_R} kappa_s e^{-(2s - NB) pos},
     // kappa_s = e^{Gamma_s + Gamma_{NB-s} - w_{NB-s} span}.  Terms in units of
     // 2^Emax, Emax the largest exponent over S (warp 0 computes the tile
-    // constants; the barrier also orders the backward states before the
-    // combine reads them).
+    // constants; later barriers order them before the combine).
     if (w == 0) {
         int kapk = 0;
         V kapm = V(0);
@@ -921,121 +927,108 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
             sm.fast = (em - en <= 60) ? 1 : 0;
         }
     }
-    __syncthreads();
-    const int Emax = sm.emax;
-    const bool fast = (sm.fast != 0);
     double base = 0.0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) base += beta[k];
     {
         V rr[NS][NB];
-        static_for<1, NS>([&](auto tc) {
-            constexpr int T = decltype(tc)::value;
-            static_for<0, NB>([&](auto kc) {
-                constexpr int k = decltype(kc)::value;
-                if constexpr ((T >> k) & 1) rr[T][k] = pow2i<V>(PF.e[T ^ (1 << k)] - PF.e[T]);
-            });
-        });
+        R::ratios(PF, rr);
         V f[NS];
 #pragma unroll
         for (int S = 0; S < NS; ++S) f[S] = x[S];
         int slot = slot0;
-#pragma unroll
+        V *F = sm.fst();
+#pragma unroll 4
         for (int c = 0; c < C; ++c) {
-            const int k = r.bt[c];
+            const int k = r.bt(c);
             if (k == -1) {
                 if (slot < JCAP) {
 #pragma unroll
-                    for (int S = 1; S < NS; ++S) sm.fst[(S - 1) * JCAP + slot] = f[S];
-                    sm.tpe[slot] = r.pe[c];
+                    for (int S = 1; S < NS; ++S) F[(S - 1) * JCAP + slot] = f[S];
+                    sm.tpe[slot] = r.pe(c);
                 }
                 ++slot;
             }
-            V fc[NB + 1];
+            V fc[NB + 1], fe[NB + 1][NB];
             r.template facs<true>(c, PF, fc);
-            static_for<1, NS>([&](auto tc) {
-                constexpr int T = decltype(tc)::value;
-                V src = V(0), rat = V(0);
-                static_for<0, NB>([&](auto kc) {
-                    constexpr int kb = decltype(kc)::value;
-                    if constexpr ((T >> kb) & 1) {
-                        src = (k == kb) ? f[T ^ (1 << kb)] : src;
-                        rat = (k == kb) ? rr[T][kb] : rat;
-                    }
-                });
-                f[T] = fma(fc[popc_c(T)] * rat, src, f[T]);
-            });
+            onehot<NB, V>(k, fc, fe);
+            R::inject(f, fe, rr);
         }
     }
-    __syncthreads();   // forward states of every target slot in sm.fst / sm.tpe
+    __syncthreads();   // forward and backward states of every target slot in shared memory
+    const int Emax = sm.emax;
+    const bool fast = (sm.fast != 0);
     // ---- combine, by target slot ---------------------------------------------
-    for (int sl = tid; sl < min(ntarget, JCAP); sl += NT) {
-        // e^{-(2s - NB) pos} = pe^{NB - 2s}
-        V q[NB + 1];
-        {
-            const V p1 = sm.tpe[sl], m1 = V(1) / p1;
-            static_for<0, NB + 1>([&](auto sc) {
-                constexpr int s = decltype(sc)::value;
-                constexpr int e = NB - 2 * s;
-                V v = V(1);
-                if constexpr (e > 0) {
+    {
+        const V *G = sm.gst();
+        const V *F = sm.fst();
+        for (int sl = tid; sl < min(ntarget, JCAP); sl += NT) {
+            // e^{-(2s - NB) pos} = pe^{NB - 2s}
+            V q[NB + 1];
+            {
+                const V p1 = sm.tpe[sl], m1 = V(1) / p1;
+                static_for<0, NB + 1>([&](auto sc) {
+                    constexpr int s = decltype(sc)::value;
+                    constexpr int e = NB - 2 * s;
+                    V v = V(1);
+                    if constexpr (e > 0) {
 #pragma unroll
-                    for (int t = 0; t < e; ++t) v *= p1;
-                } else if constexpr (e < 0) {
+                        for (int t = 0; t < e; ++t) v *= p1;
+                    } else if constexpr (e < 0) {
 #pragma unroll
-                    for (int t = 0; t < -e; ++t) v *= m1;
-                }
-                q[s] = v;
-            });
-        }
-        V sum = V(0);
-        int E = 0;
-        if (fast) {
-#pragma unroll
-            for (int S = 0; S < NS; ++S) {
-                const V fS = (S == 0) ? V(1) : sm.fst[(S - 1) * JCAP + sl];
-                const V gS = (S == FULLS) ? V(1) : sm.buf[((FULLS ^ S) - 1) * JCAP + sl];
-                sum = fma(fS * gS, sm.csc[S] * q[popc_c(S)], sum);
+                        for (int t = 0; t < -e; ++t) v *= m1;
+                    }
+                    q[s] = v;
+                });
             }
-            if (!(sum >= pow2neg<V>(-100))) sum = V(0);
-        }
-        if (sum == V(0)) {
-            // exact: every term as mantissa x 2^exponent
-            int Em = INT_MIN / 2;
+            V sum = V(0);
+            int E = 0;
+            if (fast) {
 #pragma unroll
-            for (int S = 0; S < NS; ++S) {
-                const V fS = (S == 0) ? V(1) : sm.fst[(S - 1) * JCAP + sl];
-                const V gS = (S == FULLS) ? V(1) : sm.buf[((FULLS ^ S) - 1) * JCAP + sl];
-                const Sf<V> fm = sf_make<V>(fS);
-                const Sf<V> gm = sf_make<V>(gS);
-                if (fm.m != V(0) && gm.m != V(0)) {
-                    const V z = fm.m * gm.m * sm.kap[popc_c(S)] * q[popc_c(S)];
-                    const int Ez = fm.k + gm.k + sm.esx[S];
-                    if (Ez > Em) {
-                        sum = fma(sum, pow2neg<V>(Em - Ez), z);
-                        Em = Ez;
-                    } else {
-                        sum = fma(z, pow2neg<V>(Ez - Em), sum);
+                for (int S = 0; S < NS; ++S) {
+                    const V fS = (S == 0) ? V(1) : F[(S - 1) * JCAP + sl];
+                    const V gS = (S == FULLS) ? V(1) : G[((FULLS ^ S) - 1) * JCAP + sl];
+                    sum = fma(fS * gS, sm.csc[S] * q[popc_c(S)], sum);
+                }
+                if (!(sum >= pow2neg<V>(-100))) sum = V(0);
+            }
+            if (sum == V(0)) {
+                // exact: every term as mantissa x 2^exponent
+                int Em = INT_MIN / 2;
+#pragma unroll
+                for (int S = 0; S < NS; ++S) {
+                    const V fS = (S == 0) ? V(1) : F[(S - 1) * JCAP + sl];
+                    const V gS = (S == FULLS) ? V(1) : G[((FULLS ^ S) - 1) * JCAP + sl];
+                    const Sf<V> fm = sf_make<V>(fS);
+                    const Sf<V> gm = sf_make<V>(gS);
+                    if (fm.m != V(0) && gm.m != V(0)) {
+                        const V z = fm.m * gm.m * sm.kap[popc_c(S)] * q[popc_c(S)];
+                        const int Ez = fm.k + gm.k + sm.esx[S];
+                        if (Ez > Em) {
+                            sum = fma(sum, pow2neg<V>(Em - Ez), z);
+                            Em = Ez;
+                        } else {
+                            sum = fma(z, pow2neg<V>(Ez - Em), sum);
+                        }
                     }
                 }
+                E = (sum > V(0)) ? Em : 0;
             }
-            E = (sum > V(0)) ? Em : 0;
+            // ln M = base + (Emax + lme) ln 2 + ln(lmx), lmx in [0.5, 1) (0: M = 0);
+            // the binary exponent is split off so that the logarithm is taken of
+            // a mantissa
+            V mx = V(0);
+            int me = 0;
+            if (sum > V(0)) {
+                const Sf<V> sm2 = sf_make<V>(sum);
+                mx = sm2.m;
+                me = E + sm2.k;
+            }
+            sm.lmx[sl] = mx;
+            sm.lme[sl] = me;
         }
-        // ln M = base + (Emax + lme) ln 2 + ln(lmx), lmx in [0.5, 1) (0: M = 0);
-        // the binary exponent is split off so that the logarithm is taken of
-        // a mantissa
-        V mx = V(0);
-        int me = 0;
-        if (sum > V(0)) {
-            const Sf<V> sm2 = sf_make<V>(sum);
-            mx = sm2.m;
-            me = E + sm2.k;
-        }
-        sm.lmx[sl] = mx;
-        sm.lme[sl] = me;
     }
     __syncthreads();   // ln M of every target slot in sm.lmx / sm.lme
-
     // ---- epilogue, by target slot (coalesced over the target's local indices)
     const int ntg = min(ntarget, JCAP);
     const double eps_b = tile_eps(a, b);
@@ -1111,29 +1104,65 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
             if constexpr (sizeof(V) == 4)
                 sm.lme[sl] = __float_as_int(lp);
             else
-                sm.buf[sl] = lp;   // the backward states are no longer read
+                sm.area[sl] = lp;   // the backward states are no longer read
         }
         __syncthreads();
-        // into the lanes' registers (next target's operators) and the streams
+        // into the lanes' points (next target's operators) and the streams
         V *ephi = static_cast<V *>(a.ephi);
         V *lphi = static_cast<V *>(a.lphi);
         int slot = slot0;
-#pragma unroll
+#pragma unroll 4
         for (int c = 0; c < C; ++c) {
-            if (r.bt[c] == -1) {
+            if (r.bt(c) == -1) {
                 if (slot < JCAP) {
                     const V e = sm.lmx[slot];
                     V lp;
                     if constexpr (sizeof(V) == 4)
                         lp = __int_as_float(sm.lme[slot]);
                     else
-                        lp = sm.buf[slot];
-                    r.ph[c] = e;
+                        lp = sm.area[slot];
+                    r.set_ph(c, e);
                     ephi[t0 + i0 + c] = e;
                     lphi[ts + i0 + c] = lp;
                 }
                 ++slot;
             }
+        }
+    } else if (a.mode == MODE_OBJ) {
+        // the plan marginal marg = phi_j M_j and the tile's sums of the
+        // objective terms (Eq. k-mmot distance): mass, L1 error, g marg, g mu
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int sl = tid; sl < ntg; sl += NT) {
+            const int i = off + sl;
+            const double gg = a.gj[i];
+            const double mu = a.muj[i];
+            const V mx = sm.lmx[sl];
+            double marg = 0.0;
+            if (gg != -INFINITY && mx > V(0))
+                marg = exp_acc<V>(gg * inv_eps_b + (base2 + (double)sm.lme[sl] * kLn2 + (double)vlog<V>(mx)));
+            acc[0] += marg;
+            acc[1] += fabs(marg - mu);
+            if (gg != -INFINITY) {
+                acc[2] += gg * marg;
+                acc[3] += gg * mu;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(FULL, acc[q], o);
+        }
+        __syncthreads();   // sm.area is free
+        double *red = reinterpret_cast<double *>(sm.area);   // [4][NW]
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q * NW + w] = acc[q];
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double t = 0.0;
+            for (int q = 0; q < NW; ++q) t += red[tid * NW + q];
+            a.part4[(size_t)b * 4 + tid] = t;
         }
     } else if (a.mode == MODE_RESIDUAL) {
         double acc = 0.0;
@@ -1173,31 +1202,33 @@ __global__ void __launch_bounds__(NT, sizeof(V) == 4 ? 2 : 1) k_tile(SweepArgs a
 
     // ---- operators of the next target from the new potentials --------------
     if (a.mode == MODE_UPDATE && a.jnext >= 0) {
-        __syncthreads();   // the combine no longer reads sm.buf; new beta_j written
+        __syncthreads();   // the epilogue no longer reads sm.area; new beta_j written
         tile_ops_body<NB, V, NT, C, JCAP>(r, sm, a, b, a.jnext);
     }
 }
 
 
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V>
 cudaError_t launch_tile_impl(const SweepArgs &a, cudaStream_t st)
 {
-    auto kern = k_tile<NB, V, NT, C, JCAP>;
-    const size_t sz = sizeof(TileSm<NB, V, NT, JCAP>);
+    using TS = TShape<NB, V>;
+    auto kern = k_tile<NB, V, TS::NT, TS::C, TS::JCAP>;
+    const size_t sz = sizeof(TileSm<NB, V, TS::NT, TS::C, TS::JCAP>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
     if (e != cudaSuccess) return e;
-    kern<<<a.nt, NT, sz, st>>>(a);
+    kern<<<a.nt, TS::NT, sz, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NB, typename V, int NT, int C, int JCAP>
+template <int NB, typename V>
 cudaError_t launch_tops_impl(const SweepArgs &a, cudaStream_t st)
 {
-    auto kern = k_tops<NB, V, NT, C, JCAP>;
-    const size_t sz = sizeof(TileSm<NB, V, NT, JCAP>);
+    using TS = TShape<NB, V>;
+    auto kern = k_tops<NB, V, TS::NT, TS::C, TS::JCAP>;
+    const size_t sz = sizeof(TileSm<NB, V, TS::NT, TS::C, TS::JCAP>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
     if (e != cudaSuccess) return e;
-    kern<<<a.nt, NT, sz, st>>>(a);
+    kern<<<a.nt, TS::NT, sz, st>>>(a);
     return cudaGetLastError();
 }
 

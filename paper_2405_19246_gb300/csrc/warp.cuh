@@ -129,6 +129,115 @@ struct WarpRun {
         }
     }
 
+    // ---- chunk frame (fast path) ---------------------------------------------
+    // Over a chunk of 32 points every state T is kept as an FP32/FP64 value v
+    // relative to a fixed power of two 2^E_T: E_T bounds what T can reach in
+    // the chunk, the largest own exponent of the states U inside T from which
+    // the chunk's marginals (cbits) lead to T, plus 5 bits per level of growth
+    // (32 injections at most, each factor <= 1).  An injection is then one
+    // FMA with the precomputed ratio 2^{E_{T\k} - E_T}.  A chunk in which some
+    // state's own value would sit more than 2^-90 below its frame (sources
+    // far larger than the state itself, sparse supports at small eps) runs
+    // with exact scaled floats instead.
+    static constexpr int kHead = 5 * NB + 2;
+
+    __device__ __forceinline__ bool chunk_frame(int cbits, int (&E)[NQ], V (&v)[NQ], V (&rt)[NQ][NB])
+    {
+        int e[NQ], m[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            e[q] = (f[q].m == V(0)) ? INT_MIN / 2 : f[q].k;
+            m[q] = e[q];
+        }
+        // max over the subsets reachable through the chunk's marginals
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            if ((cbits >> b) & 1) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    int src;
+                    if constexpr (b < 5) {
+                        src = __shfl_xor_sync(FULL, m[q], 1 << b);
+                    } else {
+                        src = m[0];
+#pragma unroll
+                        for (int q2 = 0; q2 < NQ; ++q2)
+                            if (q2 == (q ^ (1 << (b - 5)))) src = m[q2];
+                    }
+                    if (((lane + 32 * q) >> b) & 1) m[q] = max(m[q], src);
+                }
+            }
+        });
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            E[q] = m[q] + kHead;
+            if (f[q].m != V(0) && E[q] - e[q] > 90) bad = true;
+        }
+        if (__any_sync(FULL, bad)) return false;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] = (f[q].m == V(0)) ? V(0) : f[q].m * pow2neg<V>(e[q] - E[q]);
+        // ratios of the injections 2^{E_{T\k} - E_T}
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                int es;
+                if constexpr (b < 5) {
+                    es = __shfl_xor_sync(FULL, E[q], 1 << b);
+                } else {
+                    es = E[0];
+#pragma unroll
+                    for (int q2 = 0; q2 < NQ; ++q2)
+                        if (q2 == (q ^ (1 << (b - 5)))) es = E[q2];
+                }
+                const int d = es - E[q];
+                rt[q][b] = (((lane + 32 * q) >> b) & 1) ? ((d <= 0) ? pow2neg<V>(d) : vldexp<V>(V(1), d)) : V(0);
+            }
+        });
+        return true;
+    }
+
+    // one injection of bit K in the chunk frame
+    template <int K>
+    __device__ __forceinline__ void inject_frame(V (&v)[NQ], const V (&rt)[NQ][NB], const V *fr)
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            V src;
+            if constexpr (K < 5) {
+                src = __shfl_xor_sync(FULL, v[q], 1 << K);
+            } else {
+                src = v[0];
+#pragma unroll
+                for (int q2 = 0; q2 < NQ; ++q2)
+                    if (q2 == (q ^ (1 << (K - 5)))) src = v[q2];
+            }
+            if (((lane + 32 * q) >> K) & 1) v[q] = fma(fr[__popc(lane + 32 * q)] * rt[q][K], src, v[q]);
+        }
+    }
+
+    template <int K = 0>
+    __device__ __forceinline__ void inject_frame_dispatch(int k, V (&v)[NQ], const V (&rt)[NQ][NB], const V *fr)
+    {
+        if constexpr (K < NB) {
+            if (k == K)
+                inject_frame<K>(v, rt, fr);
+            else
+                inject_frame_dispatch<K + 1>(k, v, rt, fr);
+        }
+    }
+
+    __device__ __forceinline__ void frame_out(const int (&E)[NQ], const V (&v)[NQ])
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            Sf<V> t = sf_make<V>(v[q]);
+            if (t.m != V(0)) t.k += E[q];
+            f[q] = t;
+        }
+    }
+
     // Walk the tile's n points in processing order; on_target(slot, p) at the
     // target points with the states before the point.  bits of the marginals:
     // m < j -> m, m > j -> m - 1, target j -> -1.  fb: this warp's 32 x 16
@@ -154,16 +263,36 @@ struct WarpRun {
             }
             chunk_facs(lp, pp, bit >= 0, fb);
             const int cnt = min(32, n - c0);
-            for (int i = 0; i < cnt; ++i) {
-                const int k = __shfl_sync(FULL, bit, i);
-                if (k == -1) {
-                    const V p = __shfl_sync(FULL, pp, i);
-                    const int slot = fwd ? seen : ntarget - 1 - seen;
-                    on_target(slot, p);
-                    ++seen;
-                    continue;
+            const int cbits = __reduce_or_sync(FULL, bit >= 0 ? (1 << bit) : 0);
+            int E[NQ];
+            V v[NQ];
+            V rt[NQ][NB];
+            if (chunk_frame(cbits, E, v, rt)) {
+                for (int i = 0; i < cnt; ++i) {
+                    const int k = __shfl_sync(FULL, bit, i);
+                    if (k == -1) {
+                        frame_out(E, v);
+                        const V p = __shfl_sync(FULL, pp, i);
+                        const int slot = fwd ? seen : ntarget - 1 - seen;
+                        on_target(slot, p);
+                        ++seen;
+                        continue;
+                    }
+                    inject_frame_dispatch(k, v, rt, fb[i]);
                 }
-                inject(k, fb[i]);
+                frame_out(E, v);
+            } else {
+                for (int i = 0; i < cnt; ++i) {
+                    const int k = __shfl_sync(FULL, bit, i);
+                    if (k == -1) {
+                        const V p = __shfl_sync(FULL, pp, i);
+                        const int slot = fwd ? seen : ntarget - 1 - seen;
+                        on_target(slot, p);
+                        ++seen;
+                        continue;
+                    }
+                    inject(k, fb[i]);
+                }
             }
             __syncwarp();   // the next chunk overwrites fb
         }
@@ -309,6 +438,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     V qmax = V(-INFINITY);
     bool bad = false;
     double racc = 0.0;
+    double oacc[4] = {0.0, 0.0, 0.0, 0.0};   // MODE_OBJ: mass, L1 error, g marg, g mu
     rf.run(a, t0, n, a.j, true, nt, fbuf, [&](int slot, V pF) {
         const V pG = rb.span - pF;
         // per-level factor exp(gamma^F_s + gamma^G_{NB-s} - w_s pF - w_{NB-s} pG)
@@ -368,6 +498,16 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
                 const double gg = a.gj[i];
                 const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
                 racc += fabs(marg - a.muj[i]);
+            } else if (a.mode == MODE_OBJ) {
+                const double gg = a.gj[i];
+                const double mu = a.muj[i];
+                const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
+                oacc[0] += marg;
+                oacc[1] += fabs(marg - mu);
+                if (gg != -INFINITY) {
+                    oacc[2] += gg * marg;
+                    oacc[3] += gg * mu;
+                }
             } else if (a.mode == MODE_OUT_M) {
                 a.out[i] = (lnM == -INFINITY) ? 0.0 : exp(lnM);
             } else if (a.mode == MODE_OUT_PLAN) {
@@ -402,6 +542,11 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
         }
     } else if (a.mode == MODE_RESIDUAL) {
         if (lane == 0) a.partial[b] = racc;
+    } else if (a.mode == MODE_OBJ) {
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a.part4[(size_t)b * 4 + q] = oacc[q];
+        }
     }
 }
 

@@ -1,9 +1,11 @@
 """Failure paths, in forms that fault and hang no GPU.
 
 * A bounded inter-tile wait that runs out: the test hook MMOT_OPT_TEST_HOLD
-  keeps the first chunk of the carry scan from publishing its flags, so the
+  keeps the first chunk of the carry scans from publishing its flags, so the
   waits of the later chunks reach their (short) poll limit; the call returns
-  MMOT_ERR_TIMEOUT and the context stays usable for the next plan.
+  MMOT_ERR_TIMEOUT and the context stays usable for the next plan.  The
+  products (carry scan for l <= 5, level scans for l >= 6) and, for l = 4,
+  the objective sweeps are covered.
 * A potential update that becomes infinite: every potential of one marginal
   set to -inf (zero scaling) makes the other products zero, so the update
   ln mu - ln M is +inf: MMOT_ERR_NONFINITE.
@@ -46,6 +48,10 @@ def test_bounded_wait_times_out(Plan, l, N):
     with pytest.raises(nat.MmotError) as ei:
         plan.sinkhorn_step(1)
     assert ei.value.status == 5
+    if l <= 4:
+        with pytest.raises(nat.MmotError) as ei:
+            plan.objective()
+        assert ei.value.status == 5
     # the hook off again: the same plan and a fresh one give correct products
     plan.set_option(nat.MMOT_OPT_TEST_HOLD, 0)
     plan.reset_potentials()

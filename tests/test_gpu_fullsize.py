@@ -221,3 +221,27 @@ def test_stopping_residual(Plan, prec, l, N, eps):
     tol = 4 * _tol(prec, np.array([1.0]), xs, eps, l) * scale
     assert abs(got - ref) <= tol, (prec, got, ref, tol)
     plan.close()
+
+
+# ---- the FP32 path reaches the 1e-6 stopping tolerance -----------------------
+
+@pytest.mark.parametrize("inst", [14, 34, 38])
+def test_fp32_solve_reaches_1e6_and_matches_fp64(Plan, inst):
+    """Instances of the batched workload (l uniform in 3..8, N and eps
+    log-uniform): the FP32-scan solve stops at residual <= 1e-6 (Algorithm 1's
+    stopping test), and its transport cost, mass and dual agree with the
+    all-FP64 GPU solve at the same tolerance."""
+    l, N, eps = wl.batched_instance_params(64)[inst]
+    xs, mus = wl.batched_instance(inst, l, N)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        plan = Plan(xs, mus, eps, precision=prec)
+        out[prec] = plan.solve(1e-6, 20000)
+        plan.close()
+    for prec in ("fp32", "fp64"):
+        assert out[prec]["converged"], (prec, out[prec])
+        assert out[prec]["residual"] <= 1e-6, (prec, out[prec])
+    a, b = out["fp32"], out["fp64"]
+    assert abs(a["W"] - b["W"]) <= 1e-5 * abs(b["W"]), (a["W"], b["W"])
+    assert abs(a["mass"] - b["mass"]) <= 1e-5, (a["mass"], b["mass"])
+    assert abs(a["dual"] - b["dual"]) <= 1e-5 * abs(b["dual"]) + 1e-9, (a["dual"], b["dual"])
