@@ -176,6 +176,71 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
  * by existing plans is not affected.  bytes < 0: MMOT_ERR_INVALID_ARG. */
 mmot_status mmot_set_memory_limit(int64_t bytes);
 
+/* Device memory the library holds right now for all live plans and batches
+ * (the quantity the cap above bounds), in bytes.  bytes == NULL:
+ * MMOT_ERR_INVALID_ARG. */
+mmot_status mmot_memory_in_use(int64_t *bytes);
+
+/* ---- Shards of one instance -------------------------------------------------
+ * One instance split into P shards: contiguous ranges of the merged order of
+ * all support points (sorted by x, then marginal, then index), each held by
+ * its own plan (one GPU each in a multi-GPU run; several plans on one GPU to
+ * validate).  Every point of every marginal inside a range stays with its
+ * shard, so the potentials never move; what crosses a cut is the vector of
+ * the 2^(l-1) forward (or backward) subset states of Sec. 4.2 at the cut.
+ * Those states are linear in the states entering a range, so each shard
+ * reduces its range to a transfer operator (mmot_shard_operator); the
+ * operators of all shards (at most 2 l 2^(l-1) numbers each) are exchanged,
+ * composed in shard order with the decay exp(-w_s gap/eps) across each gap
+ * between neighbouring shards (w_s = s(l - s)), and give every shard its
+ * entering states (mmot_shard_set_inflow) before its products.  A Sinkhorn
+ * update of marginal k (Gauss-Seidel, Algorithm 1) then runs shard-locally
+ * (mmot_shard_update), and the stopping residual is the sum of the shards'
+ * terms (mmot_shard_residual).  l <= 5 (tile operators).
+ *
+ * States are indexed by bit masks T over the marginals other than the
+ * target k, bit b standing for marginal b if b < k and b + 1 otherwise; T = 0
+ * is the empty state (always 1).
+ *
+ * mmot_shard_create: as mmot_plan_create for the shard's points (N[k] >= 1
+ * points of every marginal, the shard's weights mu need not sum to 1), with
+ * N_total the sizes of the whole instance (the initial potentials are
+ * g_k = -eps ln N_total[k]).  l > 5: MMOT_ERR_RANGE.  mmot_sinkhorn_step,
+ * mmot_solve and mmot_objective reject shard plans (MMOT_ERR_INVALID_ARG);
+ * mmot_marginal works and uses the inflow when it was set for its target.
+ *
+ * mmot_shard_operator: for target k and the current potentials, writes
+ * lnop[2][l][2^(l-1)] (host or device memory, natural logarithms, -inf for
+ * 0).  lnop[0][s][U], U != 0: the factor with which a forward state S of
+ * level |S| = s at the shard's left end x_L (before its first point) reaches
+ * S + U at its right end x_R (after its last point) through the shard's
+ * points of the marginals in U; it depends on s and U only (Sec. 4.2: the
+ * rates of the levels passed and the injections).  lnop[0][s][0] = -w_s
+ * (x_R - x_L)/eps, the decay of a state that picks up nothing.  lnop[1] is
+ * the same for the backward states, from x_R to x_L.  Entries with
+ * s + |U| > l - 1 are -inf.
+ *
+ * mmot_shard_set_inflow: the states entering the shard for target k, as
+ * natural logarithms: lnF[T] the forward states at x_L, lnG[T] the backward
+ * states at x_R, 2^(l-1) host values each (entry 0 ignored; NULL: nothing
+ * enters from that side, the first or last shard).  NaN or +inf:
+ * MMOT_ERR_INVALID_ARG.  Kept until the next call; products for other
+ * targets see no inflow.
+ *
+ * mmot_shard_update: the potential update of marginal k on the shard's
+ * points (Eq. of the update in Algorithm 1) with the inflow set for k
+ * (else MMOT_ERR_INVALID_ARG).
+ *
+ * mmot_shard_residual: sum over the shard's points of marginal k of
+ * |phi_k M_k - mu_k| with the inflow set for k, into *res (host). */
+mmot_status mmot_shard_create(int l, const int64_t *N, const double *const *x, const double *const *mu,
+                              const int64_t *N_total, double eps, mmot_precision prec, int inputs_on_device,
+                              void *cuda_stream, mmot_plan *out);
+mmot_status mmot_shard_operator(mmot_plan p, int k, double *lnop);
+mmot_status mmot_shard_set_inflow(mmot_plan p, int k, const double *lnF, const double *lnG);
+mmot_status mmot_shard_update(mmot_plan p, int k);
+mmot_status mmot_shard_residual(mmot_plan p, int k, double *res);
+
 /* One marginal product without any device memory allocation.
  *
  * The paper has no counterpart to this call; it serves callers that cannot

@@ -30,7 +30,8 @@ MMOT_OPT_TEST_HOLD = 5
 EXPORTED = [
     "mmot_plan_create", "mmot_marginal", "mmot_sinkhorn_step", "mmot_solve", "mmot_objective",
     "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
-    "mmot_get_profile", "mmot_get_info", "mmot_set_memory_limit", "mmot_marginal_noalloc",
+    "mmot_get_profile", "mmot_get_info", "mmot_set_memory_limit", "mmot_memory_in_use", "mmot_marginal_noalloc",
+    "mmot_shard_create", "mmot_shard_operator", "mmot_shard_set_inflow", "mmot_shard_update", "mmot_shard_residual",
     "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_freeze", "mmot_batch_status",
     "mmot_batch_get_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
     "mmot_destroy", "mmot_last_error",
@@ -86,7 +87,13 @@ def lib():
         L.mmot_get_profile.argtypes = [vp, i, P(i64), P(d), i]
         L.mmot_get_info.argtypes = [vp, P(MmotPlanInfo)]
         L.mmot_set_memory_limit.argtypes = [i64]
+        L.mmot_memory_in_use.argtypes = [ctypes.POINTER(i64)]
         L.mmot_marginal_noalloc.argtypes = [i, P(i64), P(vp), P(vp), d, i, i, vp, vp]
+        L.mmot_shard_create.argtypes = [i, P(i64), P(vp), P(vp), P(i64), d, i, i, vp, P(vp)]
+        L.mmot_shard_operator.argtypes = [vp, i, vp]
+        L.mmot_shard_set_inflow.argtypes = [vp, i, vp, vp]
+        L.mmot_shard_update.argtypes = [vp, i]
+        L.mmot_shard_residual.argtypes = [vp, i, P(d)]
         L.mmot_batch_create.argtypes = [i, P(i), P(i64), P(vp), P(vp), P(d), i, i, vp, P(vp)]
         L.mmot_batch_step.argtypes = [vp, i, d, P(i)]
         L.mmot_batch_reset.argtypes = [vp]

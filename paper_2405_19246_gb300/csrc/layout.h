@@ -156,9 +156,11 @@ inline void append_layout(HostLayout &D, const HostLayout &S, const int64_t *mar
 // (forward: left ends, backward: right ends), s = 0..NB, as scaled floats
 // m * 2^k stored as float2 (k in the bits of .y) or double2.  The decay out
 // of the last tile, and across the boundary between two instances of a batch
-// (seg, one entry per tile, may be empty), is 0: no state crosses it.
+// (seg, one entry per tile, may be empty), is 0: no state crosses it.  With
+// to_end (shards of one instance) the last tile in processing order decays
+// to the range's own end instead (forward x_R, backward x_L).
 inline void decay_tables(const HostLayout &L, int NB, bool fp64, std::vector<unsigned char> &F,
-                         std::vector<unsigned char> &B, const std::vector<int32_t> &seg = {})
+                         std::vector<unsigned char> &B, const std::vector<int32_t> &seg = {}, bool to_end = false)
 {
     const int nt = L.nt;
     const int l = L.l;
@@ -188,12 +190,13 @@ inline void decay_tables(const HostLayout &L, int NB, bool fp64, std::vector<uns
     for (int b = 0; b < nt; ++b) {
         const bool okF = (b + 1 < nt) && same(b, b + 1);
         const bool okB = (b >= 1) && same(b - 1, b);
-        const double dF = okF ? L.ulb[b + 1] - L.ulb[b] : 0.0;
-        const double dB = okB ? L.urb[b] - L.urb[b - 1] : 0.0;
+        const bool endF = to_end && b + 1 == nt, endB = to_end && b == 0;
+        const double dF = okF ? L.ulb[b + 1] - L.ulb[b] : (endF ? L.span[b] : 0.0);
+        const double dB = okB ? L.urb[b] - L.urb[b - 1] : (endB ? L.span[b] : 0.0);
         for (int s = 0; s < NB1; ++s) {
             const double ws = (double)s * (double)(l - s);
-            put(F, (size_t)b * NB1 + s, okF ? -ws * dF : -INFINITY);
-            put(B, (size_t)b * NB1 + s, okB ? -ws * dB : -INFINITY);
+            put(F, (size_t)b * NB1 + s, (okF || endF) ? -ws * dF : -INFINITY);
+            put(B, (size_t)b * NB1 + s, (okB || endB) ? -ws * dB : -INFINITY);
         }
     }
 }

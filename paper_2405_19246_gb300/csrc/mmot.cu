@@ -118,6 +118,10 @@ struct InstanceIn {
     const double *const *x = nullptr;
     const double *const *mu = nullptr;
     double eps = 0.0;
+    // shards of one instance: the sizes of the whole instance (initial
+    // potentials -eps ln N_total); the shard's weights need not sum to 1
+    const int64_t *Ntot = nullptr;
+    double init_count(int k) const { return (double)(Ntot ? Ntot[k] : N[k]); }
 };
 
 struct mmot_plan_s {
@@ -137,6 +141,13 @@ struct mmot_plan_s {
     int spin_limit = 1 << 23;
     int use_graph = 1;
     int hold = 0;           // test hook (MMOT_OPT_TEST_HOLD)
+    // shard of one instance (mmot_shard_create): states entering the range
+    // for target inflow_target ([2][NS] scaled floats), composed operator out
+    bool shard = false;
+    int64_t Ninit[MMOT_MAXL] = {0};
+    unsigned char *inflow = nullptr;
+    int inflow_target = -1;
+    double *d_lnop = nullptr;   // [2][NB+1][NS]
     int64_t dev_bytes = 0;  // device memory held by this plan
     // host copies needed to re-centre potentials
     std::vector<uint8_t> h_mid;
@@ -184,6 +195,7 @@ struct mmot_plan_s {
     unsigned char *agg = nullptr, *inc = nullptr, *bcarry = nullptr;
     unsigned char *fcarry = nullptr, *opF = nullptr, *opB = nullptr;
     unsigned char *pdecF = nullptr, *pdecB = nullptr;
+    unsigned char *coef = nullptr;   // level passes (l >= 6): per tile and marginal, level-to-level coefficients
     int *cflags = nullptr;          // carry-scan chunk flags
     size_t cflags_n = 0;
     unsigned char *cagg = nullptr;  // carry-scan chunk contributions [2][32][NS]
@@ -304,6 +316,25 @@ cudaError_t launch_levels(int NB, const SweepArgs &a, bool fp64, cudaStream_t st
     }
 }
 
+template <int NB>
+cudaError_t launch_opc_nb(const SweepArgs &a, bool fp64, cudaStream_t st, double *lnop)
+{
+    if constexpr (NB <= kMaxOpBits)
+        return fp64 ? launch_opcompose<NB, double>(a, st, lnop) : launch_opcompose<NB, float>(a, st, lnop);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_opc(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, double *lnop)
+{
+    switch (NB) {
+    case 1: return launch_opc_nb<1>(a, fp64, st, lnop);
+    case 2: return launch_opc_nb<2>(a, fp64, st, lnop);
+    case 3: return launch_opc_nb<3>(a, fp64, st, lnop);
+    case 4: return launch_opc_nb<4>(a, fp64, st, lnop);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_ops(int NB, const SweepArgs &a, bool fp64, cudaStream_t st, int kind)
 {
     return mmot::launch_three_phase(NB, a, fp64, st, kind);
@@ -407,12 +438,14 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.seg = p->d_seg;
     a.teps = p->d_teps;
     a.frozen = p->d_frozen;
+    a.inflow = (p->shard && j < p->l && p->inflow_target == j) ? p->inflow : nullptr;
+    a.shard_end = (p->shard && j < p->l) ? 1 : 0;
     return a;
 }
 
 // kernels per marginal product in an iteration: carry scan + tile products
 // (three-phase, l <= 5), or 2 (NB levels x contribution + scan) + products
-int launches_per_product(mmot_plan p) { return p->three_phase ? 2 : 4 * p->NB + 1; }
+int launches_per_product(mmot_plan p) { return p->three_phase ? 2 : 2 * ((p->NB + 1) / 2 + p->NB) + 1; }
 
 // kernel ids: 2 k_tops, 3 k_carry, 4 k_tile (three-phase design, l <= 5);
 // 5 k_wpass, 6 k_lscan, 4 k_wprod (level passes and warp tiles, l >= 6);
@@ -467,17 +500,29 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
         if (a.jnext >= 0) p->ops_target = a.jnext;
         return MMOT_OK;
     }
-    // level passes: backward and forward carries level by level, then the
-    // tile products with both carries known
+    // level passes: backward and forward carries two levels per walk (the
+    // pass of level lv also gives level lv+1 its share that does not go
+    // through a level-lv carry), one scan per level, then the tile products
+    // with both carries known
     CUDA_TRY(cudaMemsetAsync(p->cflags, 0, sizeof(int) * p->cflags_n, p->st));
+    a.coef = p->coef;
     for (int fwd = 0; fwd < 2; ++fwd) {
-        for (int lv = 1; lv <= p->NB; ++lv) {
+        for (int lv = 1; lv <= p->NB; lv += 2) {
+            const bool pair = (lv + 1 <= p->NB);
+            a.pair = pair ? 1 : 0;
             mmot_status s = timed_launch(p, 5, a, fp64, lv, fwd);
             if (s != MMOT_OK) return s;
+            a.pair = 0;
             s = timed_launch(p, 6, a, fp64, lv, fwd);
             if (s != MMOT_OK) return s;
+            if (pair) {
+                a.pair = 1;
+                s = timed_launch(p, 6, a, fp64, lv + 1, fwd);
+                if (s != MMOT_OK) return s;
+            }
         }
     }
+    a.pair = 0;
     return timed_launch(p, 4, a, fp64);
 }
 
@@ -703,9 +748,11 @@ mmot_status check_device_error(mmot_plan p)
     CUDA_TRY(cudaStreamSynchronize(p->st));
     if (h) {
         CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->st));
-        if (h & ERR_TIMEOUT) return fail(MMOT_ERR_TIMEOUT, "an inter-tile wait reached its poll limit");
+        // a wait also gives up (and sets the timeout bit) once another error
+        // is recorded: report that error first
         if (h & ERR_RANGE) return fail(MMOT_ERR_RANGE, "a tile exceeded its target-point capacity");
         if (h & ERR_NONFINITE) return fail(MMOT_ERR_NONFINITE, "a potential became NaN or infinite");
+        if (h & ERR_TIMEOUT) return fail(MMOT_ERR_TIMEOUT, "an inter-tile wait reached its poll limit");
     }
     return MMOT_OK;
 }
@@ -863,7 +910,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
                                 (long long)i);
                 sum += m;
             }
-            if (std::fabs((double)sum - 1.0) > 1e-12)
+            if (!in.Ntot && std::fabs((double)sum - 1.0) > 1e-12)
                 return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, (double)sum);
             hmu[k].insert(hmu[k].end(), qmu[k].begin(), qmu[k].end());
             seg_off[(size_t)(q + 1) * l + k] = seg_off[(size_t)q * l + k] + n;
@@ -887,6 +934,8 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     p->eps = eps;
     p->prec = (int)prec;
     for (int k = 0; k < l; ++k) p->N[k] = N[k];
+    p->shard = (nin == 1 && ins[0].Ntot != nullptr);
+    for (int k = 0; k < l; ++k) p->Ninit[k] = (int64_t)ins[0].init_count(k);
     p->NB = l - 1;
     p->NS = 1 << p->NB;
     p->K = K;
@@ -925,7 +974,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     p->h_beta0.assign((size_t)nt * l, 0.0);
     for (int b = 0; b < nt; ++b)
         for (int k = 0; k < l; ++k)
-            p->h_beta0[(size_t)b * l + k] = -std::log((double)ins[hseg[b]].N[k]);
+            p->h_beta0[(size_t)b * l + k] = -std::log(ins[hseg[b]].init_count(k));
     p->h_beta = p->h_beta0;
 
     // ---- device allocation and upload -------------------------------------
@@ -973,6 +1022,11 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     p->cflags_n = p->three_phase ? (size_t)2 * 32 * (p->NB + 1) : (size_t)2 * p->NS * 32;
     PA(p->cflags, p->cflags_n);
     PA(p->cagg, (size_t)2 * 32 * p->NS * p->sfsz);
+    if (!p->three_phase) PA(p->coef, (size_t)nt * p->NB * p->sfsz);
+    if (p->shard) {
+        PA(p->inflow, (size_t)2 * p->NS * p->sfsz);
+        PA(p->d_lnop, (size_t)2 * (p->NB + 1) * p->NS);
+    }
     if (p->three_phase) {
         PA(p->opF, (size_t)nt * p->NB * p->NS * p->sfsz);
         PA(p->opB, (size_t)nt * p->NB * p->NS * p->sfsz);
@@ -1040,7 +1094,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     std::vector<unsigned char> hdecF, hdecB;
     const std::vector<int32_t> segv = batch ? hseg : std::vector<int32_t>();
     if (l <= kMaxOpBits || l == 8) decay_tables(L, l, fp64, p->h_odecF, p->h_odecB, segv);
-    decay_tables(L, p->NB, fp64, hdecF, hdecB, segv);
+    decay_tables(L, p->NB, fp64, hdecF, hdecB, segv, p->shard);
     ce = ce ? ce : up(p->pdecF, hdecF.data(), hdecF.size());
     ce = ce ? ce : up(p->pdecB, hdecB.data(), hdecB.size());
     ce = ce ? ce : up(p->span, hspan.data(), sizeof(double) * nt);
@@ -1051,7 +1105,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     for (int k = 0; k < l && ce == cudaSuccess; ++k) {
         hg[k].resize(N[k]);
         for (int q = 0; q < nin; ++q) {
-            const double g0 = -ins[q].eps * std::log((double)ins[q].N[k]);
+            const double g0 = -ins[q].eps * std::log(ins[q].init_count(k));
             for (int64_t i = seg_off[(size_t)q * l + k]; i < seg_off[(size_t)(q + 1) * l + k]; ++i) hg[k][i] = g0;
         }
         hlm[k].resize(N[k]);
@@ -1063,7 +1117,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     if (batch) {
         std::vector<double> g0((size_t)nin * l);
         for (int q = 0; q < nin; ++q)
-            for (int k = 0; k < l; ++k) g0[(size_t)q * l + k] = -ins[q].eps * std::log((double)ins[q].N[k]);
+            for (int k = 0; k < l; ++k) g0[(size_t)q * l + k] = -ins[q].eps * std::log(ins[q].init_count(k));
         ce = ce ? ce : up(p->d_seg, hseg.data(), sizeof(int32_t) * nt);
         ce = ce ? ce : up(p->d_teps, hteps.data(), sizeof(double) * nt);
 
@@ -1228,6 +1282,7 @@ mmot_status mmot_marginal(mmot_plan p, int k, int plan_marginal, double *out)
 mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out)
 {
     if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
+    if (p->shard) return fail(MMOT_ERR_INVALID_ARG, "shard plans iterate through mmot_shard_update");
     if (n_iters < 0) return fail(MMOT_ERR_INVALID_ARG, "n_iters < 0");
     if (n_iters > 0) {
         mmot_status s0 = ensure_ops(p, 0);
@@ -1272,6 +1327,7 @@ mmot_status mmot_sinkhorn_step(mmot_plan p, int n_iters, double *residual_out)
 mmot_status mmot_objective(mmot_plan p, mmot_result *out)
 {
     if (!p || !out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or out");
+    if (p->shard) return fail(MMOT_ERR_INVALID_ARG, "not on a shard plan");
     memset(out, 0, sizeof(*out));
     std::vector<mmot_result> R;
     mmot_status s = plan_objective(p, R);
@@ -1283,6 +1339,7 @@ mmot_status mmot_objective(mmot_plan p, mmot_result *out)
 mmot_status mmot_solve(mmot_plan p, double tol, int itr_max, mmot_result *out)
 {
     if (!p || !out) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or out");
+    if (p->shard) return fail(MMOT_ERR_INVALID_ARG, "shard plans iterate through mmot_shard_update");
     if (itr_max < 0) return fail(MMOT_ERR_INVALID_ARG, "itr_max < 0");
     int t = 0;
     double res = INFINITY;
@@ -1373,7 +1430,7 @@ mmot_status mmot_reset_potentials(mmot_plan p)
         if (p->batch)
             k_reset_seg<<<p->nseg, 256, 0, p->st>>>(p->g[k], p->d_goff, p->d_g0, k, l);
         else
-            k_reset<<<64, 256, 0, p->st>>>(p->g[k], p->N[k], -p->eps * std::log((double)p->N[k]));
+            k_reset<<<64, 256, 0, p->st>>>(p->g[k], p->N[k], -p->eps * std::log((double)p->Ninit[k]));
         CUDA_TRY(cudaGetLastError());
         p->launches += 1;
     }
@@ -1438,6 +1495,116 @@ mmot_status mmot_set_memory_limit(int64_t bytes)
     if (bytes < 0) return fail(MMOT_ERR_INVALID_ARG, "memory limit < 0");
     g_mem_limit = bytes;
     return MMOT_OK;
+}
+
+mmot_status mmot_memory_in_use(int64_t *bytes)
+{
+    if (!bytes) return fail(MMOT_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = g_mem_used.load();
+    return MMOT_OK;
+}
+
+// ---- shards of one instance ----------------------------------------------------
+
+mmot_status mmot_shard_create(int l, const int64_t *N, const double *const *x, const double *const *mu,
+                              const int64_t *N_total, double eps, mmot_precision prec, int inputs_on_device,
+                              void *cuda_stream, mmot_plan *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(MMOT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (l < 2 || l > MMOT_MAXL) return fail(MMOT_ERR_INVALID_ARG, "l = %d outside [2, 8]", l);
+    if (!N || !x || !mu || !N_total) return fail(MMOT_ERR_INVALID_ARG, "N, x, mu or N_total is NULL");
+    if (l - 1 > kMaxOpBits) return fail(MMOT_ERR_RANGE, "shards need l <= %d (tile operators), got l = %d", kMaxOpBits + 1, l);
+    for (int k = 0; k < l; ++k)
+        if (N_total[k] < N[k])
+            return fail(MMOT_ERR_INVALID_ARG, "N_total[%d] = %lld < N[%d] = %lld", k, (long long)N_total[k], k,
+                        (long long)N[k]);
+    std::vector<InstanceIn> ins(1);
+    ins[0].N = N;
+    ins[0].x = x;
+    ins[0].mu = mu;
+    ins[0].eps = eps;
+    ins[0].Ntot = N_total;
+    return plan_build(l, ins, prec, inputs_on_device, cuda_stream, out);
+}
+
+mmot_status mmot_shard_operator(mmot_plan p, int k, double *lnop)
+{
+    if (!p || !lnop) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or lnop");
+    if (!p->shard) return fail(MMOT_ERR_INVALID_ARG, "not a shard plan");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    mmot_status s = ensure_ops(p, k);
+    if (s != MMOT_OK) return s;
+    SweepArgs a = make_args(p, k, MODE_UPDATE, nullptr);
+    CUDA_TRY(launch_opc(p->NB, a, p->prec == MMOT_FP64, p->st, p->d_lnop));
+    p->launches += 1;
+    const size_t n = (size_t)2 * (p->NB + 1) * p->NS;
+    CUDA_TRY(cudaMemcpyAsync(lnop, p->d_lnop, sizeof(double) * n, cudaMemcpyDefault, p->st));
+    return check_device_error(p);
+}
+
+mmot_status mmot_shard_set_inflow(mmot_plan p, int k, const double *lnF, const double *lnG)
+{
+    if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
+    if (!p->shard) return fail(MMOT_ERR_INVALID_ARG, "not a shard plan");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    const int NS = p->NS;
+    const bool fp64 = (p->prec == MMOT_FP64);
+    std::vector<unsigned char> h((size_t)2 * NS * p->sfsz, 0);
+    for (int d = 0; d < 2; ++d) {
+        const double *src = d ? lnG : lnF;
+        for (int T = 1; T < NS; ++T) {
+            const double y = src ? src[T] : -INFINITY;
+            if (std::isnan(y) || y == INFINITY)
+                return fail(MMOT_ERR_INVALID_ARG, "inflow %s[%d] is not finite or -inf", d ? "lnG" : "lnF", T);
+            if (y == -INFINITY) continue;
+            // m 2^e with m in [0.5, 1): e = floor(y / ln 2) + 1
+            const double t = y / std::log(2.0);
+            const double n = std::floor(t);
+            int e = 0;
+            const double m = std::frexp(std::exp2(t - n), &e);
+            const long long kk = (long long)n + e;
+            if (fp64) {
+                double *q = reinterpret_cast<double *>(h.data()) + 2 * ((size_t)d * NS + T);
+                q[0] = m;
+                q[1] = (double)kk;
+            } else {
+                float *q = reinterpret_cast<float *>(h.data()) + 2 * ((size_t)d * NS + T);
+                const int ki = (int)kk;
+                q[0] = (float)m;
+                std::memcpy(&q[1], &ki, sizeof(int));
+            }
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(p->inflow, h.data(), h.size(), cudaMemcpyHostToDevice, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    p->inflow_target = k;
+    return MMOT_OK;
+}
+
+mmot_status mmot_shard_update(mmot_plan p, int k)
+{
+    if (!p) return fail(MMOT_ERR_INVALID_ARG, "NULL plan");
+    if (!p->shard) return fail(MMOT_ERR_INVALID_ARG, "not a shard plan");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    if (p->inflow_target != k) return fail(MMOT_ERR_INVALID_ARG, "no inflow set for marginal %d", k);
+    mmot_status s = enqueue_product(p, k, MODE_UPDATE, nullptr, (k + 1) % p->l);
+    if (s != MMOT_OK) return s;
+    return check_device_error(p);
+}
+
+mmot_status mmot_shard_residual(mmot_plan p, int k, double *res)
+{
+    if (!p || !res) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or res");
+    if (!p->shard) return fail(MMOT_ERR_INVALID_ARG, "not a shard plan");
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    if (p->inflow_target != k) return fail(MMOT_ERR_INVALID_ARG, "no inflow set for marginal %d", k);
+    mmot_status s = enqueue_residual(p, k, k + 1);
+    if (s != MMOT_OK) return s;
+    s = read_scalar(p, p->dsum, res);
+    if (s != MMOT_OK) return s;
+    return check_device_error(p);
 }
 
 // ---- batches ------------------------------------------------------------------

@@ -87,6 +87,19 @@ struct SweepArgs {
     const void *pdecF;
     const void *pdecB;
     int jnext;                // target of the operators computed after an update (-1: none)
+    // level passes of l >= 6 taking two levels per walk: the pass of level s
+    // also leaves level s+1's contributions that do not go through a level-s
+    // carry, and per tile and marginal the coefficient with which a level-s
+    // carry reaches level s+1 (coef, [nt*NB] scaled floats); the scan of
+    // level s+1 adds the carries' share (pair = 1 in both launches)
+    void *coef;
+    int pair;
+    // shards of one instance (shard.cuh): the states entering the range
+    // ([dir][NS] scaled floats, absolute, at the left end forward and the right
+    // end backward; null: only the empty state), and whether the last tile in
+    // processing order carries its operator and decay to the range's end
+    const void *inflow;
+    int shard_end;
     // carry scan over chunks of tiles: flags [2][G][NB+1], contributions [2][G][NS]
     int *cflags;
     void *cagg;
@@ -122,6 +135,10 @@ template <int NB, typename V>
 cudaError_t launch_lagg(const SweepArgs &a, cudaStream_t s, int level, int fwd);
 template <int NB, typename V>
 cudaError_t launch_lscan(const SweepArgs &a, cudaStream_t s, int level, int fwd);
+// Transfer operator of a whole shard from the tile operators (shard.cuh):
+// lnop[2][NB + 1][2^NB] natural logarithms, device memory.
+template <int NB, typename V>
+cudaError_t launch_opcompose(const SweepArgs &a, cudaStream_t s, double *lnop);
 constexpr int kMaxOpBits = 4;
 // message for mmot_last_error (defined in mmot.cu)
 }  // namespace mmot

@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(256) k_lscan(SweepArgs a, int SL, int fwd_i)
         }
         ++q;
     }
-    const SfT<V> *__restrict__ own = sfp<V>(a.agg);
+    const SfT<V> *own = sfp<V>(a.agg);   // written in pass 1 of a two-level scan
     const SfT<V> *__restrict__ pdec = sfp<V>(fwd ? a.pdecF : a.pdecB);
     SfT<V> *E = sfp<V>(fwd ? a.fcarry : a.bcarry);
     const int slot = ((fwd ? 0 : 1) * NS + T) * 32;
@@ -1120,12 +1120,23 @@ __global__ void __launch_bounds__(256) k_lscan(SweepArgs a, int SL, int fwd_i)
     __shared__ int s_ak[NWB], s_bk[NWB];
     __shared__ V s_em;
     __shared__ int s_ek;
-    // pass 1: this thread's map x -> am x + bb
+    // pass 1: this thread's map x -> am x + bb (the second level of a
+    // two-level pass first adds the share of the previous level's carries,
+    // E[T \ m] coef[m], to the stored contribution)
     Sf<V> am = Sf<V>{V(0.5), 1}, bb = sf_zero<V>();
     for (int v = v0; v < v1; ++v) {
         const int b = tile_of(v);
         const Sf<V> dec = sf_load<V>(__ldg(pdec + (size_t)b * (NB + 1) + SL));
-        const Sf<V> o = sf_load<V>(__ldcg(own + (size_t)b * NS + T));
+        Sf<V> o = sf_load<V>(__ldcg(own + (size_t)b * NS + T));
+        if (a.pair) {
+#pragma unroll
+            for (int m = 0; m < NB; ++m) {
+                if (!((T >> m) & 1)) continue;
+                const Sf<V> eu = sf_load<V>(__ldcg(E + (size_t)b * NS + (T ^ (1 << m))));
+                if (eu.m != V(0)) o = sf_add(o, sf_mul(eu, sf_load<V>(__ldcg(sfp<V>(a.coef) + (size_t)b * NB + m))));
+            }
+            sfp<V>(a.agg)[(size_t)b * NS + T] = sf_store(o);   // read again by pass 2
+        }
         bb = sf_mul(sf_add(bb, o), dec);
         am = sf_mul(am, dec);
     }
@@ -1432,6 +1443,15 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
             }
             if (__ballot_sync(FULL, fail)) {
                 if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+            }
+            // states entering the range (shards): at the first tile's base
+            if (a.inflow && lane == 0) {
+                const double d0 = fabs(ub - chunk_base(0));
+#pragma unroll
+                for (int T = 1; T < NS; ++T)
+                    if (popc_c(T) == s)
+                        part[T] = sf_add(part[T], sf_scale_exp(sf_load<V>(sfp<V>(a.inflow)[(fwd ? 0 : 1) * NS + T]),
+                                                               -ws * d0));
             }
 #pragma unroll
             for (int T = 1; T < NS; ++T) {

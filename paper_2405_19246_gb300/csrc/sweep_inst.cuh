@@ -4,6 +4,7 @@
 #include "sweep.cuh"
 #include "warp.cuh"
 #include "tile.cuh"
+#include "shard.cuh"
 
 // launchers of the three-phase design, defined for NB <= kMaxOpBits
 #define MMOT_INSTANTIATE_OPS(NB_, V_)                                                  \
@@ -22,6 +23,11 @@
     cudaError_t launch_carry<NB_, V_>(const SweepArgs &a, cudaStream_t s)              \
     {                                                                                  \
         return launch_carry_impl<NB_, V_>(a, s);                                       \
+    }                                                                                  \
+    template <>                                                                        \
+    cudaError_t launch_opcompose<NB_, V_>(const SweepArgs &a, cudaStream_t s, double *o)\
+    {                                                                                  \
+        return launch_opcompose_impl<NB_, V_>(a, s, o);                                \
     }                                                                                  \
     }
 

@@ -675,10 +675,16 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP> &r, Ti
     if (b + 1 < a.nt) {
         dF = a.ulb[b + 1] - a.ulb[b];
         cutF = a.seg && a.seg[b + 1] != a.seg[b];
+    } else if (a.shard_end) {
+        dF = a.urb[b] - a.ulb[b];   // to the range's right end
+        cutF = false;
     }
     if (b >= 1) {
         dB = a.urb[b] - a.urb[b - 1];
         cutB = a.seg && a.seg[b - 1] != a.seg[b];
+    } else if (a.shard_end) {
+        dB = a.urb[0] - a.ulb[0];   // to the range's left end
+        cutB = false;
     }
     for (int t = tid; t < 2 * NOP; t += NT) {
         const int dir = t / NOP, e = t % NOP;

@@ -37,6 +37,8 @@ struct WarpRun {
     double gam[NB + 1];  // gamma_s = D_1 + ... + D_s
     V span;
     int lane;
+    int coef_level = 0;   // > 0: lane m sums the level-coef_level factors of the points of bit m
+    V coef_acc = V(0);
 
     __device__ static constexpr int rate(int s) { return s * (L - s); }
 
@@ -74,14 +76,15 @@ struct WarpRun {
         return g;
     }
 
-    // states from absolute carries (levels below maxlev; the rest 0)
+    // states from absolute carries (levels below maxlev; the rest 0; the
+    // empty state 1, the source of the level-1 injections)
     __device__ void load_carries(const SfT<V> *carry, int b, const double *beta, int maxlev)
     {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int T = lane + 32 * q;
             const int s = __popc(T);
-            f[q] = sf_zero<V>();
+            f[q] = (T == 0) ? Sf<V>{V(0.5), 1} : sf_zero<V>();
             if (T != 0 && s < maxlev)
                 f[q] = sf_scale_exp(sf_load<V>(carry[(size_t)b * NS + T]), -(sum_beta(beta, T) + gam_at(s)));
         }
@@ -278,6 +281,7 @@ struct WarpRun {
                         ++seen;
                         continue;
                     }
+                    if (coef_level && lane == k) coef_acc += fb[i][coef_level];
                     inject_frame_dispatch(k, v, rt, fb[i]);
                 }
                 frame_out(E, v);
@@ -291,6 +295,7 @@ struct WarpRun {
                         ++seen;
                         continue;
                     }
+                    if (coef_level && lane == k) coef_acc += fb[i][coef_level];
                     inject(k, fb[i]);
                 }
             }
@@ -374,13 +379,29 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
     WarpRun<NB, V, LM> r;
     r.init(a, b);
     r.load_carries(sfp<V>(fwd ? a.fcarry : a.bcarry), b, beta, SL);
+    const bool pair = a.pair && SL < NB;
+    r.coef_level = pair ? SL + 1 : 0;
     r.run(a, t0, n, a.j, fwd, 0, fbuf[threadIdx.x >> 5], [](int, V) {});
 #pragma unroll
     for (int q = 0; q < WarpRun<NB, V, LM>::NQ; ++q) {
         const int T = r.lane + 32 * q;
-        if (popc_c(T) == SL)
+        const int s = popc_c(T);
+        if (s == SL || (pair && s == SL + 1))
             sfp<V>(a.agg)[(size_t)b * NS + T] =
-                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V, LM>::sum_beta(beta, T) + r.gam_at(SL)));
+                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V, LM>::sum_beta(beta, T) + r.gam_at(s)));
+    }
+    if (pair && r.lane < NB) {
+        // a level-SL carry U reaches U + {m} with exp(beta_m + D_{SL+1}) times
+        // the sum of the level-(SL+1) factors of the points of marginal m
+        V dn = V(0);
+#pragma unroll
+        for (int s = 1; s <= NB; ++s)
+            if (s == SL + 1) dn = r.D[s];
+        double bm = 0.0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if (k == r.lane) bm = beta[k];
+        sfp<V>(a.coef)[(size_t)b * NB + r.lane] = sf_store(sf_scale_exp(sf_make<V>(r.coef_acc), bm + (double)dn));
     }
 }
 

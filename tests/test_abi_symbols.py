@@ -75,3 +75,7 @@ def test_memory_limit_arguments_without_gpu():
     assert L.mmot_set_memory_limit(-1) == 1
     assert b"memory limit" in L.mmot_last_error()
     assert L.mmot_set_memory_limit(0) == 0
+    used = ctypes.c_int64(-1)
+    assert L.mmot_memory_in_use(ctypes.byref(used)) == 0
+    assert used.value == 0   # no plan exists in this process
+    assert L.mmot_memory_in_use(None) == 1

@@ -13,6 +13,7 @@
 * A device-memory cap below what a plan needs: MMOT_ERR_OOM before any
   allocation crosses it, and the next creation without the cap succeeds.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -94,18 +95,24 @@ def test_memory_limit_gives_oom(Plan):
     from paper_2405_19246_gb300 import _native as nat
     xs, mus = wl.sorted_uniform_lognormal(l=4, N=5000, instance=91)
     L = nat.lib()
-    need = None
+    used = ctypes.c_int64()
     plan = Plan(xs, mus, 1e-2, precision="fp32")
     need = plan.info()["device_bytes"]
     plan.close()
     assert need > 0
+    # the cap counts what other live plans of this process hold as well
+    assert L.mmot_memory_in_use(ctypes.byref(used)) == 0
+    base = used.value
     try:
-        assert L.mmot_set_memory_limit(need // 2) == 0
+        assert L.mmot_set_memory_limit(base + need // 2) == 0
         with pytest.raises(nat.MmotError) as ei:
             Plan(xs, mus, 1e-2, precision="fp32")
         assert ei.value.status == 3   # MMOT_ERR_OOM
-        assert L.mmot_set_memory_limit(need + (1 << 20)) == 0
+        assert L.mmot_memory_in_use(ctypes.byref(used)) == 0
+        assert used.value == base   # the failed creation freed what it took
+        assert L.mmot_set_memory_limit(base + need + (1 << 20)) == 0
         plan = Plan(xs, mus, 1e-2, precision="fp32")
+        assert plan.info()["device_bytes"] == need
         plan.close()
     finally:
         L.mmot_set_memory_limit(0)
