@@ -42,6 +42,10 @@ WORKLOADS = {
     "wide": dict(l=8, N=1 << 24, eps=1e-4, iters=2, gen="dirichlet",
                  desc="l=8, N=2^24 per marginal, sorted U[0,1] supports, Dirichlet(1) weights, "
                       "eps=1e-4, 2 Sinkhorn iterations per solve"),
+    "wide-small": dict(l=8, N=1 << 16, eps=0.0256, iters=2, gen="dirichlet",
+                       desc="l=8, N=2^16 per marginal, sorted U[0,1] supports, Dirichlet(1) weights, "
+                            "eps=0.0256 (the points per eps of the N=2^24, eps=1e-4 workload), "
+                            "2 Sinkhorn iterations per solve"),
     "grid": dict(l=3, N=1000, eps=1e-2, iters=200, gen="grid",
                  desc="l=3, N=1000 uniform grid, Gaussian-mixture weights, eps=1e-2, 200 iterations"),
 }
@@ -56,7 +60,7 @@ NCU_TRAFFIC = {
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "tile.cuh", "shapes.cuh", "mmot_internal.cuh"):
+    for f in ("sweep.cuh", "tile.cuh", "warp.cuh", "shapes.cuh", "mmot_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2405_19246_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -212,6 +216,13 @@ def run_ours(args, w, rank, world, local_rank):
     stats = plan.profile_stats(reset=True)
     plan.profile(False)
 
+    # the first product and the potentials after one iteration from phi = 1/N
+    # (compared with the oracle's in the CPU-baseline leg)
+    plan.reset_potentials()
+    lnM0 = plan.marginal(0, "lnM")
+    plan.sinkhorn_step(1)
+    g1 = [plan.get_potentials(k) for k in range(w["l"])]
+
     # end-to-end through the public API from host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -225,7 +236,7 @@ def run_ours(args, w, rank, world, local_rank):
     d2h = sum(g.nbytes for g in gout)
     plan.close()
     return dict(ms=t_max, out=out, info=info, stats=stats, clocks=clocks, launches=launches,
-                e2e_s=e2e_s, h2d=h2d, d2h=d2h, xs=xs_h, mus=mus_h)
+                e2e_s=e2e_s, h2d=h2d, d2h=d2h, xs=xs_h, mus=mus_h, lnM0=lnM0, g1=g1)
 
 
 def oracle_iteration_sample(w, xs, mus):
@@ -235,12 +246,15 @@ def oracle_iteration_sample(w, xs, mus):
     eps = w["eps"]
     gs = [np.full(len(x), -eps * math.log(len(x))) for x in xs]
     n_prod = w["l"]
+    lnM0 = None
     t0 = time.perf_counter()
     for j in range(n_prod):
         lnM = oracle.marginal_subset(xs, gs, eps, j)
+        if j == 0:
+            lnM0 = lnM
         gs[j] = oracle.potential_update(mus[j], lnM, eps)
     dt = time.perf_counter() - t0
-    return (n_prod / w["l"]) / dt, dt, n_prod
+    return (n_prod / w["l"]) / dt, dt, n_prod, lnM0, gs
 
 
 def batched_instances(count, seed_offset=0):
@@ -487,14 +501,35 @@ def main():
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "algorithmic_bytes_per_launch": bytes_dom, "avg_launch_us": avg * 1e6,
                 "kernels": per_kernel, "kernel_source": src_hash}
+    if w["l"] >= 6:
+        # l >= 6: the state walks bind, not HBM.  Algorithmic work: a point of
+        # marginal m adds to the 2^(l-2) states containing m, one FMA each, in
+        # each walk over the tile (k_wpass: one walk; k_wprod: a backward and
+        # a forward walk plus 2^(l-1) products per target in the combine).
+        # Peak: 152 SMs x 128 FP32 FMA per clock x the maximum SM clock.
+        half = 1 << (w["l"] - 2)
+        fma = {"k_wpass": T * half, "k_wprod": 2 * T * half + w["N"] * (2 * half)}
+        peak_alu = 152 * 128 * 2.07e9 / 1e12
+        ach = fma[dom] / avg / 1e12 if dom in fma and avg > 0 else None
+        roofline = dict(roofline, bound="alu", achieved=ach, peak=peak_alu, unit="TFMA/s",
+                        peak_kind="derived: 152 SMs x 128 FP32 FMA/clock x 2.07 GHz",
+                        frac=(ach / peak_alu) if ach else None, algorithmic_fma_per_launch=fma.get(dom),
+                        hbm={"achieved_gbs": achieved, "peak_gbs": peak,
+                             "frac": (achieved / peak) if achieved else None})
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        v, dt, nprod = oracle_iteration_sample(w, r["xs"], r["mus"])
+        v, dt, nprod, lnM0, g1 = oracle_iteration_sample(w, r["xs"], r["mus"])
+        fin = np.isfinite(lnM0)
+        lnm_err = float(np.max(np.abs(r["lnM0"][fin] - lnM0[fin])))
+        g_err = max(float(np.max(np.abs(a[np.isfinite(b)] - b[np.isfinite(b)]))) for a, b in zip(r["g1"], g1))
         cpu = {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
                "sample": "one Sinkhorn iteration (%d marginal products with updates) of the same "
-                         "instance from phi=1/N, FP64 subset chains, single thread: %.2f s" % (nprod, dt)}
+                         "instance from phi=1/N, FP64 subset chains, single thread: %.2f s" % (nprod, dt),
+               "parity": {"max_abs_lnM_err": lnm_err, "max_abs_potential_err_over_eps": g_err / w["eps"],
+                          "what": "GPU vs oracle on this sample: ln M_1 at phi = 1/N (all %d points) and "
+                                  "every potential after the iteration, divided by eps" % w["N"]}}
     e2e_value = w["iters"] / r["e2e_s"]
     line = {"metric": metric, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,

@@ -196,6 +196,7 @@ struct mmot_plan_s {
     unsigned char *fcarry = nullptr, *opF = nullptr, *opB = nullptr;
     unsigned char *pdecF = nullptr, *pdecB = nullptr;
     unsigned char *coef = nullptr;   // level passes (l >= 6): per tile and marginal, level-to-level coefficients
+    void *lops = nullptr;            // tile kernels (l <= 5): lanes' chunk operators of the current target
     int *cflags = nullptr;          // carry-scan chunk flags
     size_t cflags_n = 0;
     unsigned char *cagg = nullptr;  // carry-scan chunk contributions [2][32][NS]
@@ -364,6 +365,23 @@ void shape_nb(bool fp64, int *K, int *NT, int *JCAP)
     }
 }
 
+// lanes' chunk operators of one tile (tile.cuh): [dir][entry][lane]
+int64_t tile_lops_bytes(int NB, bool fp64)
+{
+    int nop = 0;
+    for (int s = 0; s < NB; ++s)
+        for (int U = 1; U < (1 << NB); ++U)
+            if (s + __builtin_popcount(U) <= NB) ++nop;
+    int nt = 0;
+    switch (NB) {
+    case 1: nt = fp64 ? TShape<1, double>::NT : TShape<1, float>::NT; break;
+    case 2: nt = fp64 ? TShape<2, double>::NT : TShape<2, float>::NT; break;
+    case 3: nt = fp64 ? TShape<3, double>::NT : TShape<3, float>::NT; break;
+    default: nt = fp64 ? TShape<4, double>::NT : TShape<4, float>::NT; break;
+    }
+    return (int64_t)2 * nop * nt * (fp64 ? 8 : 4);
+}
+
 int tile_jcap(int NB, bool fp64)
 {
     switch (NB) {
@@ -439,6 +457,7 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.teps = p->d_teps;
     a.frozen = p->d_frozen;
     a.inflow = (p->shard && j < p->l && p->inflow_target == j) ? p->inflow : nullptr;
+    a.lops = (j < p->l) ? p->lops : nullptr;
     a.shard_end = (p->shard && j < p->l) ? 1 : 0;
     return a;
 }
@@ -1030,6 +1049,11 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     if (p->three_phase) {
         PA(p->opF, (size_t)nt * p->NB * p->NS * p->sfsz);
         PA(p->opB, (size_t)nt * p->NB * p->NS * p->sfsz);
+        {
+            unsigned char *lo = nullptr;
+            PA(lo, (size_t)nt * tile_lops_bytes(p->NB, fp64));
+            p->lops = lo;
+        }
         // padded stream: every tile starts on a 16-element boundary
         p->h_toff.resize(nt);
         int64_t o = 0;

@@ -100,6 +100,9 @@ struct SweepArgs {
     // processing order carries its operator and decay to the range's end
     const void *inflow;
     int shard_end;
+    // tile kernels (l <= 5): every lane's chunk transfer operators of the
+    // current target, [tile][dir][entry][lane] (null: recomputed by a walk)
+    void *lops;
     // carry scan over chunks of tiles: flags [2][G][NB+1], contributions [2][G][NS]
     int *cflags;
     void *cagg;

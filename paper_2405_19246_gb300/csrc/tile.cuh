@@ -291,6 +291,7 @@ struct TileSm {
     // does not fit the instruction cache)
     alignas(16) V pph[C * NT];   // scaled phi
     V ppe[C * NT];               // e^{pos}
+    V ppm[C * NT];               // e^{-pos} (one division per point and kernel)
     uint8_t pmd[C * NT];         // marginal (0xff: padding)
     __device__ V *gst() { return area; }
     __device__ V *fst() { return area + GSZ; }
@@ -323,6 +324,7 @@ struct TileRun {
 
     __device__ __forceinline__ V ph(int c) const { return sp->pph[c * NT + tid]; }
     __device__ __forceinline__ V pe(int c) const { return sp->ppe[c * NT + tid]; }
+    __device__ __forceinline__ V pm(int c) const { return sp->ppm[c * NT + tid]; }
     __device__ __forceinline__ void set_ph(int c, V v) { sp->pph[c * NT + tid] = v; }
     __device__ __forceinline__ int mid_of(int c) const { return sp->pmd[c * NT + tid]; }
     __device__ __forceinline__ static int bit_of(int m, int j) { return (m == 0xff) ? -2 : (m == j ? -1 : (m < j ? m : m - 1)); }
@@ -348,6 +350,7 @@ struct TileRun {
 #pragma unroll
                 for (int e = 0; e < PV; ++e) {
                     sp->ppe[(q * PV + e) * NT + tid] = pu[e];
+                    sp->ppm[(q * PV + e) * NT + tid] = V(1) / pu[e];
                     sp->pph[(q * PV + e) * NT + tid] = pv[e];
                 }
             }
@@ -361,6 +364,7 @@ struct TileRun {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 sp->ppe[c * NT + tid] = V(1);
+                sp->ppm[c * NT + tid] = V(1);
                 sp->pph[c * NT + tid] = V(0);
                 sp->pmd[c * NT + tid] = 0xff;
             }
@@ -374,7 +378,7 @@ struct TileRun {
     __device__ __forceinline__ void facs(int c, const PassC<NB, V> &P, V (&f)[NB + 1]) const
     {
         const V pc = pe(c);
-        const V pinv = V(1) / pc;
+        const V pinv = pm(c);
         const V up = FWD ? pc : pinv;
         const V dn = FWD ? pinv : pc;
         const V up2 = up * up, dn2 = dn * dn;
@@ -427,19 +431,31 @@ struct TileRun {
     // P.e) from the tile carries.  cu: on lane T < NS, the carry of state T in
     // the unscaled tile frame (carry e^{-(sum beta_T + Gamma_|T|)}).
     template <bool FWD>
-    __device__ __forceinline__ void chunk_starts(Sm &sm, PassC<NB, V> &P, const Sf<V> cu, V (&x)[NS], int bits)
+    __device__ __forceinline__ void chunk_starts(Sm &sm, PassC<NB, V> &P, const Sf<V> cu, V (&x)[NS], int bits,
+                                                 const V *lop)
     {
         __syncthreads();   // the previous pass has finished reading sm.wsum
-        // 1. chunk operator
+        // 1. chunk operator: stored by the walk that computed the tile
+        // operators of this target (lop: [entry][lane]), else one walk
         V op[NB][NS];
         op_zero<NB, V>(op);
+        if (lop) {
+            static_for<0, NB>([&](auto scc) {
+                constexpr int s = decltype(scc)::value;
+                static_for<1, NS>([&](auto vc) {
+                    constexpr int U = decltype(vc)::value;
+                    if constexpr (op_ok<NB>(s, U)) op[s][U] = lop[op_index<NB>(s, U) * NT + tid];
+                });
+            });
+        } else {
 #pragma unroll 4
-        for (int i = 0; i < C; ++i) {
-            const int c = FWD ? i : C - 1 - i;
-            V f[NB + 1], fe[NB + 1][NB];
-            facs<FWD>(c, P, f);
-            onehot<NB, V>(bt(c), f, fe);
-            op_push_right<NB, V>(op, fe);
+            for (int i = 0; i < C; ++i) {
+                const int c = FWD ? i : C - 1 - i;
+                V f[NB + 1], fe[NB + 1][NB];
+                facs<FWD>(c, P, f);
+                onehot<NB, V>(bt(c), f, fe);
+                op_push_right<NB, V>(op, fe);
+            }
         }
         x[0] = V(1);
         // 2. level by level
@@ -608,6 +624,9 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP> &r, Ti
             op_push_left<NB, V>(opb, fe);
         }
         V *sc = sm.area;   // [2][NOP][NT]
+        // the lanes' operators also go out for the next product of target jn
+        // (its chunk starts need no walk): [tile][dir][entry][lane]
+        V *lo = a.lops ? static_cast<V *>(a.lops) + (size_t)b * 2 * NOP * NT : nullptr;
         static_for<0, NB>([&](auto scc) {
             constexpr int s = decltype(scc)::value;
             static_for<1, NS>([&](auto vc) {
@@ -616,6 +635,10 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP> &r, Ti
                     constexpr int e = op_index<NB>(s, U);
                     sc[(0 * NOP + e) * NT + tid] = opf[s][U];
                     sc[(1 * NOP + e) * NT + tid] = opb[s][U];
+                    if (lo) {
+                        lo[(0 * NOP + e) * NT + tid] = opf[s][U];
+                        lo[(1 * NOP + e) * NT + tid] = opb[s][U];
+                    }
                 }
             });
         });
@@ -772,6 +795,9 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
     r.sp = &sm;
     r.load(a, t0, i0);
     r.set_bits(j);
+    // this tile's stored lane operators of target j (forward, then backward)
+    constexpr int NOPL = op_count<NB>();
+    const V *lops = a.lops ? static_cast<const V *>(a.lops) + (size_t)b * 2 * NOPL * NT : nullptr;
 
     // ---- target slots (rank among the tile's targets, forward order) -------
     int tcount = 0, lbits = 0;
@@ -847,7 +873,7 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
             cu = sf_load<V>(sfp<V>(a.bcarry)[(size_t)b * NS + lane]);
             cu = sf_scale_exp(cu, -(sum_beta(lane) + gam_at(lane)));
         }
-        r.template chunk_starts<false>(sm, PB, cu, x, bits);
+        r.template chunk_starts<false>(sm, PB, cu, x, bits, lops ? lops + NOPL * NT : nullptr);
     }
     {
         V rr[NS][NB];
@@ -887,7 +913,7 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
             cu = sf_load<V>(sfp<V>(a.fcarry)[(size_t)b * NS + lane]);
             cu = sf_scale_exp(cu, -(sum_beta(lane) + gam_at(lane)));
         }
-        r.template chunk_starts<true>(sm, PF, cu, x, bits);
+        r.template chunk_starts<true>(sm, PF, cu, x, bits, lops);
     }
     // Per term S: F_S G_{R\S} = f g 2^{eF_S + eB_{R\S}} e^{sum beta_R} kappa_s e^{-(2s - NB) pos},
     // kappa_s = e^{Gamma_s + Gamma_{NB-s} - w_{NB-s} span}.  Terms in units of

@@ -225,12 +225,15 @@ def test_stopping_residual(Plan, prec, l, N, eps):
 
 # ---- the FP32 path reaches the 1e-6 stopping tolerance -----------------------
 
-@pytest.mark.parametrize("inst", [14, 34, 38])
+@pytest.mark.parametrize("inst", [14, 8, 15, 58])
 def test_fp32_solve_reaches_1e6_and_matches_fp64(Plan, inst):
     """Instances of the batched workload (l uniform in 3..8, N and eps
-    log-uniform): the FP32-scan solve stops at residual <= 1e-6 (Algorithm 1's
-    stopping test), and its transport cost, mass and dual agree with the
-    all-FP64 GPU solve at the same tolerance."""
+    log-uniform), one each of l = 3, 4, 5, 6: the FP32-scan solve stops at
+    residual <= 1e-6 (Algorithm 1's stopping test), and its transport cost,
+    mass and dual agree with the all-FP64 GPU solve at the same tolerance.
+    (Instances at small eps that the FP64 solve itself does not bring to 1e-6
+    within the budget are not used: there the two precisions stall together,
+    their residuals agreeing to about 1e-5 relative.)"""
     l, N, eps = wl.batched_instance_params(64)[inst]
     xs, mus = wl.batched_instance(inst, l, N)
     out = {}
