@@ -179,6 +179,31 @@ __device__ __forceinline__ Sf<V> sf_scale_exp(Sf<V> a, double x)
     return r;
 }
 
+// A tile constant x as x log2(e) in fixed point: int64 with 32 fractional
+// bits.  Sums of such values are exact, so the scale of a state,
+// exp(sum_{m in T} beta_m + gamma_|T|), costs integer adds and one FP32 exp2
+// instead of FP64 arithmetic per state (one FP64 warp instruction occupies the
+// FP64 pipe of a sub-partition for about 64 cycles on this GPU).  Each term
+// is rounded to 2^-32, far below the FP32 mantissa.  (FP32 path only: the
+// FP64 path keeps FP64 exponents.)
+__device__ __forceinline__ long long fx_log2(double x)
+{
+    const double y = fmin(fmax(x * (kLog2e * 4294967296.0), -4.0e18), 4.0e18);
+    return __double2ll_rn(y);
+}
+
+// a * 2^(X / 2^32)
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_scale_fx(Sf<V> a, long long X)
+{
+    if (a.m == V(0)) return a;
+    const int n = (int)(X >> 32);   // floor
+    const float fr = (float)(unsigned)(X & 0xffffffffll) * 2.3283064365386963e-10f;
+    Sf<V> r = sf_make<V>(a.m * (V)exp2f(fr));
+    r.k += a.k + n;
+    return r;
+}
+
 template <typename V>
 __device__ __forceinline__ Sf<V> sf_add(Sf<V> a, Sf<V> b)
 {

@@ -273,6 +273,8 @@ struct TileSm {
     V csc[NS];            // combine: kappa_|S| 2^{E_S - Emax} of every term
     int esx[NS];          // combine: E_S - Emax
     V kap[NB + 1];        // combine: mantissas of kappa_s
+    long long fxb[NB];    // FP32 path: baselines beta_k of the bits, fixed point (fx_log2)
+    long long fxg[NB + 1];  // FP32 path: Gamma_s, fixed point
     int emax;             // combine: largest term exponent
     int fast;             // combine: every term within 2^60 of the largest
     // per target slot: ln M as mantissa (lmx) and binary exponent (lme) after
@@ -331,6 +333,41 @@ struct TileRun {
     // bit of point c for the current target: 0..NB-1, -1 target, -2 padding
     __device__ __forceinline__ int bt(int c) const { return bit_of(mid_of(c), jcur); }
     __device__ __forceinline__ void set_bits(int j) { jcur = j; }
+
+    // FP32 path: the fixed-point table of the baselines of the bits (beta, per
+    // thread in registers) and of Gamma_s, by threads 0..2 NB; the caller
+    // passes a barrier before reading it
+    __device__ __forceinline__ void fill_fx(const double (&beta)[NB]) const
+    {
+        if constexpr (sizeof(V) == 4) {
+            if (tid < NB) {
+                double bk = 0.0;
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (k == tid) bk = beta[k];
+                sp->fxb[tid] = fx_log2(bk);
+            } else if (tid <= 2 * NB) {
+                const int s = tid - NB;
+                double g = 0.0;
+#pragma unroll
+                for (int q = 1; q <= NB; ++q) {
+                    const V as = (V)arate(q) * span;
+                    if (q <= s) g += (double)(as > V(0) ? as : V(0));
+                }
+                sp->fxg[s] = fx_log2(g);
+            }
+        }
+    }
+
+    // FP32 path: a * exp(-(sum_{k in T} beta_k + Gamma_|T|)) from the table
+    __device__ __forceinline__ Sf<V> unscale_fx(Sf<V> a, int T) const
+    {
+        long long X = sp->fxg[__popc(T)];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            if ((T >> k) & 1) X += sp->fxb[k];
+        return sf_scale_fx(a, -X);
+    }
 
     // the lane's C points (e^{pos}, scaled phi, marginal) into shared memory
     __device__ __forceinline__ void load(const SweepArgs &a, uint32_t t0, int i0)
@@ -686,6 +723,10 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP> &r, Ti
         const int rt = __ldg(a.reftile + (size_t)b * l + m);
         beta[k] = *(volatile const double *)(a.beta + (size_t)rt * l + m);
     }
+    if constexpr (sizeof(V) == 4) {
+        r.fill_fx(beta);   // target jn's bits
+        __syncthreads();
+    }
     double Gam[NB + 1];
     Gam[0] = 0.0;
 #pragma unroll
@@ -726,20 +767,31 @@ __device__ __forceinline__ void tile_ops_body(TileRun<NB, V, NT, C, JCAP> &r, Ti
         });
         const V val = sm.area[((size_t)dir * NOP + e) * NT];
         const int su = s + __popc(U);
-        double bu = 0.0;
-#pragma unroll
-        for (int k = 0; k < NB; ++k)
-            if ((U >> k) & 1) bu += beta[k];
         const double d = dir ? dB : dF;
         const bool cut = dir ? cutB : cutF;
         const double wsu = (double)su * (double)(L - su);
-        double gsu = 0.0, gs = 0.0;
+        Sf<V> o = sf_zero<V>();
+        if (!cut) {
+            if constexpr (sizeof(V) == 4) {
+                long long X = sm.fxg[su] - sm.fxg[s] - fx_log2(wsu * d);
 #pragma unroll
-        for (int q = 0; q <= NB; ++q) {
-            if (q == su) gsu = Gam[q];
-            if (q == s) gs = Gam[q];
+                for (int k = 0; k < NB; ++k)
+                    if ((U >> k) & 1) X += sm.fxb[k];
+                o = sf_scale_fx(sf_make<V>(val), X);
+            } else {
+                double bu = 0.0;
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if ((U >> k) & 1) bu += beta[k];
+                double gsu = 0.0, gs = 0.0;
+#pragma unroll
+                for (int q = 0; q <= NB; ++q) {
+                    if (q == su) gsu = Gam[q];
+                    if (q == s) gs = Gam[q];
+                }
+                o = sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d);
+            }
         }
-        const Sf<V> o = cut ? sf_zero<V>() : sf_scale_exp(sf_make<V>(val), bu + gsu - gs - wsu * d);
         sfp<V>(dir ? a.opB : a.opF)[((size_t)b * NB + s) * NS + U] = sf_store(o);
     }
 }
@@ -824,6 +876,7 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
         const int rt = __ldg(a.reftile + (size_t)b * l + m);
         beta[k] = *(volatile const double *)(a.beta + (size_t)rt * l + m);
     }
+    r.fill_fx(beta);
     __syncthreads();
     int slot0 = tincl - tcount;   // first slot of this lane's targets
     int ntarget = 0;
@@ -871,7 +924,10 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
         Sf<V> cu = sf_zero<V>();
         if (lane < NS && lane > 0) {
             cu = sf_load<V>(sfp<V>(a.bcarry)[(size_t)b * NS + lane]);
-            cu = sf_scale_exp(cu, -(sum_beta(lane) + gam_at(lane)));
+            if constexpr (sizeof(V) == 4)
+                cu = r.unscale_fx(cu, lane);
+            else
+                cu = sf_scale_exp(cu, -(sum_beta(lane) + gam_at(lane)));
         }
         r.template chunk_starts<false>(sm, PB, cu, x, bits, lops ? lops + NOPL * NT : nullptr);
     }
@@ -911,7 +967,10 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
         Sf<V> cu = sf_zero<V>();
         if (lane < NS && lane > 0) {
             cu = sf_load<V>(sfp<V>(a.fcarry)[(size_t)b * NS + lane]);
-            cu = sf_scale_exp(cu, -(sum_beta(lane) + gam_at(lane)));
+            if constexpr (sizeof(V) == 4)
+                cu = r.unscale_fx(cu, lane);
+            else
+                cu = sf_scale_exp(cu, -(sum_beta(lane) + gam_at(lane)));
         }
         r.template chunk_starts<true>(sm, PF, cu, x, bits, lops);
     }

@@ -39,6 +39,9 @@ struct WarpRun {
     int lane;
     int coef_level = 0;   // > 0: lane m sums the level-coef_level factors of the points of bit m
     V coef_acc = V(0);
+    // FP32 path: this warp's fixed-point table in shared memory, [0, NB) the
+    // baselines beta_k, [NB, 2 NB] gamma_s (fx_log2)
+    long long *fx = nullptr;
 
     __device__ static constexpr int rate(int s) { return s * (L - s); }
 
@@ -52,7 +55,7 @@ struct WarpRun {
         for (int s = 1; s <= NB; ++s) {
             const V as = (V)(rate(s) - rate(s - 1));
             D[s] = (as > V(0)) ? as * span : V(0);
-            gam[s] = gam[s - 1] + (double)D[s];
+            if constexpr (sizeof(V) == 8) gam[s] = gam[s - 1] + (double)D[s];
         }
     }
 
@@ -76,6 +79,50 @@ struct WarpRun {
         return g;
     }
 
+    // FP32 path: the fixed-point table of the tile (lane k: beta_k; lanes
+    // 1..NB: D_s, then a prefix sum over the lanes for gamma_s)
+    __device__ void setup_fx(const double *beta, long long *table)
+    {
+        fx = table;
+        if constexpr (sizeof(V) == 4) {
+            double bk = 0.0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (k == lane) bk = beta[k];
+            if (lane < NB) fx[lane] = fx_log2(bk);
+            V d = V(0);
+#pragma unroll
+            for (int s = 1; s <= NB; ++s)
+                if (s == lane) d = D[s];
+            long long g = (lane >= 1 && lane <= NB) ? fx_log2((double)d) : 0ll;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const long long y = __shfl_up_sync(FULL, g, o);
+                if (lane >= o) g += y;
+            }
+            if (lane <= NB) fx[NB + lane] = g;
+            __syncwarp();
+        }
+    }
+
+    // a * exp(sign (sum_{k in T} beta_k + gamma_s))
+    __device__ __forceinline__ Sf<V> scale_state(Sf<V> a, int T, int s, bool neg, const double *beta) const
+    {
+        if constexpr (sizeof(V) == 4) {
+            long long X = 0;
+#pragma unroll
+            for (int q = 0; q <= NB; ++q)
+                if (q == s) X = fx[NB + q];
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if ((T >> k) & 1) X += fx[k];
+            return sf_scale_fx(a, neg ? -X : X);
+        } else {
+            const double x = sum_beta(beta, T) + gam_at(s);
+            return sf_scale_exp(a, neg ? -x : x);
+        }
+    }
+
     // states from absolute carries (levels below maxlev; the rest 0; the
     // empty state 1, the source of the level-1 injections)
     __device__ void load_carries(const SfT<V> *carry, int b, const double *beta, int maxlev)
@@ -85,8 +132,7 @@ struct WarpRun {
             const int T = lane + 32 * q;
             const int s = __popc(T);
             f[q] = (T == 0) ? Sf<V>{V(0.5), 1} : sf_zero<V>();
-            if (T != 0 && s < maxlev)
-                f[q] = sf_scale_exp(sf_load<V>(carry[(size_t)b * NS + T]), -(sum_beta(beta, T) + gam_at(s)));
+            if (T != 0 && s < maxlev) f[q] = scale_state(sf_load<V>(carry[(size_t)b * NS + T]), T, s, true, beta);
         }
     }
 
@@ -351,8 +397,10 @@ __device__ __forceinline__ int warp_count_targets(const SweepArgs &a, uint32_t t
     return c;
 }
 
-__device__ __forceinline__ void warp_betas(const SweepArgs &a, int b, int j, int NB, double *beta)
+template <int NB>
+__device__ __forceinline__ void warp_betas(const SweepArgs &a, int b, int j, double *beta)
 {
+#pragma unroll
     for (int k = 0; k < NB; ++k) {
         const int m = (k < j) ? k : k + 1;
         const int rt = __ldg(a.reftile + (size_t)b * a.l + m);
@@ -374,10 +422,12 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
     double beta[NB];
-    warp_betas(a, b, a.j, NB, beta);
+    warp_betas<NB>(a, b, a.j, beta);
     __shared__ V fbuf[4][32][16];
+    __shared__ long long fxt[4][2 * NB + 1];
     WarpRun<NB, V, LM> r;
     r.init(a, b);
+    r.setup_fx(beta, fxt[threadIdx.x >> 5]);
     r.load_carries(sfp<V>(fwd ? a.fcarry : a.bcarry), b, beta, SL);
     const bool pair = a.pair && SL < NB;
     r.coef_level = pair ? SL + 1 : 0;
@@ -387,8 +437,7 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
         const int T = r.lane + 32 * q;
         const int s = popc_c(T);
         if (s == SL || (pair && s == SL + 1))
-            sfp<V>(a.agg)[(size_t)b * NS + T] =
-                sf_store(sf_scale_exp(r.f[q], WarpRun<NB, V, LM>::sum_beta(beta, T) + r.gam_at(s)));
+            sfp<V>(a.agg)[(size_t)b * NS + T] = sf_store(r.scale_state(r.f[q], T, s, false, beta));
     }
     if (pair && r.lane < NB) {
         // a level-SL carry U reaches U + {m} with exp(beta_m + D_{SL+1}) times
@@ -408,7 +457,10 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
 // One tile of a marginal product (both carries known): backward pass with the
 // states at the target points in shared memory, forward pass with the
 // combine, FP64 epilogue.  One warp per block (shared memory holds the
-// backward states of up to JCAP targets).
+// backward states of up to JCAP targets).  The combine keeps each target's
+// sum as an FP32 mantissa and a binary exponent; the FP64 work (ln M, the
+// potential update, residual and objective terms) runs afterwards with one
+// target per lane.
 template <int NB, typename V>
 __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
 {
@@ -418,8 +470,11 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     constexpr int JCAP = WShape<NB, V>::JCAP;
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ SfT<V> Gt[JCAP * NS];
-    __shared__ double gq[JCAP];
+    __shared__ V tsw[JCAP];      // per target: sum mantissa (0: M = 0)
+    __shared__ int tew[JCAP];    // per target: binary exponent of the sum
+    __shared__ double gq[JCAP];  // per target: new g/eps (update)
     __shared__ V fbuf[32][16];
+    __shared__ long long fxt[2 * NB + 1];
     const int b = blockIdx.x;
     if (a.frozen && (a.mode == MODE_UPDATE || a.mode == MODE_RESIDUAL) && a.frozen[a.seg[b]]) {
         if (a.mode == MODE_RESIDUAL && threadIdx.x == 0) a.partial[b] = 0.0;
@@ -434,7 +489,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
         return;
     }
     double beta[NB];
-    warp_betas(a, b, a.j, NB, beta);
+    warp_betas<NB>(a, b, a.j, beta);
     double sb = 0.0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) sb += beta[k];
@@ -444,6 +499,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     // backward states at the target points
     R rb;
     rb.init(a, b);
+    rb.setup_fx(beta, fxt);
     rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
     rb.run(a, t0, n, a.j, false, nt, fbuf, [&](int slot, V) {
 #pragma unroll
@@ -451,28 +507,59 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     });
     __syncwarp();
 
-    // forward pass and combine: ln M = sb + E ln 2 + ln(sum), per target
+    // Per-level factor of the combine, exp(gamma_s + gamma_{NB-s} - w_s pF -
+    // w_{NB-s} pG) with pG = span - pF:  exp(K_s - a_s pF), K_s = gamma_s +
+    // gamma_{NB-s} - w_{NB-s} span, a_s = w_s - w_{NB-s}.  Lane s keeps K_s
+    // (fixed point on the FP32 path, FP64 otherwise); per target it forms
+    // a_s pF log2(e) as an exact FP32 product plus a rounded remainder.
+    const int sl_ = (lane <= NB) ? lane : 0;
+    const int as_ = R::rate(sl_) - R::rate(NB - sl_);
+    long long Kx = 0;
+    double Kd = 0.0;
+    if constexpr (sizeof(V) == 4) {
+        long long g1 = 0, g2 = 0;
+#pragma unroll
+        for (int q = 0; q <= NB; ++q) {
+            if (q == sl_) g1 = fxt[NB + q];
+            if (q == NB - sl_) g2 = fxt[NB + q];
+        }
+        Kx = g1 + g2 - fx_log2((double)R::rate(NB - sl_) * (double)rb.span);
+    } else {
+        Kd = (rb.gam_at(sl_) + rb.gam_at(NB - sl_) - (double)R::rate(NB - sl_) * (double)rb.span) * kLog2e;
+    }
+
+    // forward pass and combine, per target: sum_S F_S G_{R\S} factor_|S| as
+    // mantissa x 2^exponent into tsw / tew
     R rf;
     rf.init(a, b);
+    rf.fx = fxt;
     rf.load_carries(sfp<V>(a.fcarry), b, beta, NB + 1);
-    const int32_t off = a.cnt[(size_t)b * a.l + a.j];
-    V qmax = V(-INFINITY);
-    bool bad = false;
-    double racc = 0.0;
-    double oacc[4] = {0.0, 0.0, 0.0, 0.0};   // MODE_OBJ: mass, L1 error, g marg, g mu
     rf.run(a, t0, n, a.j, true, nt, fbuf, [&](int slot, V pF) {
-        const V pG = rb.span - pF;
-        // per-level factor exp(gamma^F_s + gamma^G_{NB-s} - w_s pF - w_{NB-s} pG)
-        // as 2^(n_s) * mu_s, computed by lane s
         int en = 0;
         V em = V(0);
         if (lane <= NB) {
-            const int s = lane;
-            const double c = (rf.gam_at(s) + rb.gam_at(NB - s) - (double)R::rate(s) * (double)pF -
-                              (double)R::rate(NB - s) * (double)pG) * kLog2e;
-            const double fl = floor(c);
-            en = (int)fl;
-            em = vexp2<V>((V)(c - fl));
+            if constexpr (sizeof(V) == 4) {
+                constexpr float L2h = 1.44269502162933349609375f;   // log2(e) rounded to FP32
+                constexpr float L2l = 1.925963033500011e-08f;       // log2(e) - L2h
+                const float af = (float)as_;
+                const float ph = af * pF;
+                const float pl = fmaf(af, pF, -ph);                 // a pF = ph + pl exactly
+                const float th = ph * L2h;
+                const float tl = fmaf(ph, L2h, -th) + fmaf(ph, L2l, pl * L2h);
+                const float nth = floorf(th);
+                const float fy = (th - nth) + tl;                  // a pF log2(e) = nth + fy
+                const int nK = (int)(Kx >> 32);
+                const float fK = (float)(unsigned)(Kx & 0xffffffffll) * 2.3283064365386963e-10f;
+                const float cf = fK - fy;
+                const float fl = floorf(cf);
+                en = nK - (int)nth + (int)fl;
+                em = exp2f(cf - fl);
+            } else {
+                const double c = Kd - (double)as_ * (double)pF * kLog2e;
+                const double fl = floor(c);
+                en = (int)fl;
+                em = vexp2<V>((V)(c - fl));
+            }
         }
         int Emax = INT_MIN / 2;
         V sum = V(0);
@@ -503,45 +590,62 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
         V sw = (sum > V(0)) ? sum * pow2neg<V>(Emax - Ew) : V(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULL, sw, o);
-        const double lnM = (sw > V(0)) ? sb + (double)Ew * kLn2 + (double)vlog<V>(sw) : -INFINITY;
         if (lane == 0) {
-            const int i = off + slot;
-            if (a.mode == MODE_UPDATE) {
-                const double lm = a.lnmuj[i];
-                double g = -INFINITY;
-                if (lm > -INFINITY) {
-                    g = lm - lnM;
-                    if (!isfinite(g)) bad = true;
-                    qmax = fmax(qmax, (V)g);
-                }
-                gq[slot] = g;
-            } else if (a.mode == MODE_RESIDUAL) {
-                const double gg = a.gj[i];
-                const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
-                racc += fabs(marg - a.muj[i]);
-            } else if (a.mode == MODE_OBJ) {
-                const double gg = a.gj[i];
-                const double mu = a.muj[i];
-                const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
-                oacc[0] += marg;
-                oacc[1] += fabs(marg - mu);
-                if (gg != -INFINITY) {
-                    oacc[2] += gg * marg;
-                    oacc[3] += gg * mu;
-                }
-            } else if (a.mode == MODE_OUT_M) {
-                a.out[i] = (lnM == -INFINITY) ? 0.0 : exp(lnM);
-            } else if (a.mode == MODE_OUT_PLAN) {
-                a.out[i] = (a.gj[i] == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(a.gj[i] * inv_eps_b + lnM);
-            } else {
-                a.out[i] = lnM;
-            }
+            tsw[slot] = sw;
+            tew[slot] = Ew;
         }
     });
+    __syncwarp();
+
+    // FP64 epilogue, one target per lane: ln M = sum of the baselines +
+    // Ew ln 2 + ln(sw)
+    const int32_t off = a.cnt[(size_t)b * a.l + a.j];
+    double qmax = -INFINITY;
+    bool bad = false;
+    double racc = 0.0;
+    double oacc[4] = {0.0, 0.0, 0.0, 0.0};   // MODE_OBJ: mass, L1 error, g marg, g mu
+    for (int slot = lane; slot < nt; slot += 32) {
+        const V sw = tsw[slot];
+        const double lnM = (sw > V(0)) ? sb + (double)tew[slot] * kLn2 + (double)vlog<V>(sw) : -INFINITY;
+        const int i = off + slot;
+        if (a.mode == MODE_UPDATE) {
+            const double lm = a.lnmuj[i];
+            double g = -INFINITY;
+            if (lm > -INFINITY) {
+                g = lm - lnM;
+                if (!isfinite(g)) bad = true;
+                qmax = fmax(qmax, (double)(V)g);
+            }
+            gq[slot] = g;
+        } else if (a.mode == MODE_RESIDUAL) {
+            const double gg = a.gj[i];
+            const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
+            racc += fabs(marg - a.muj[i]);
+        } else if (a.mode == MODE_OBJ) {
+            const double gg = a.gj[i];
+            const double mu = a.muj[i];
+            const double marg = (gg == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(gg * inv_eps_b + lnM);
+            oacc[0] += marg;
+            oacc[1] += fabs(marg - mu);
+            if (gg != -INFINITY) {
+                oacc[2] += gg * marg;
+                oacc[3] += gg * mu;
+            }
+        } else if (a.mode == MODE_OUT_M) {
+            a.out[i] = (lnM == -INFINITY) ? 0.0 : exp(lnM);
+        } else if (a.mode == MODE_OUT_PLAN) {
+            a.out[i] = (a.gj[i] == -INFINITY || lnM == -INFINITY) ? 0.0 : exp(a.gj[i] * inv_eps_b + lnM);
+        } else {
+            a.out[i] = lnM;
+        }
+    }
     if (a.mode == MODE_UPDATE) {
         // new potentials and ln phi relative to the new baseline, by lane
         // (each lane its points; the slot is the rank among the targets)
-        const double bx = isfinite((double)__shfl_sync(FULL, qmax, 0)) ? (double)__shfl_sync(FULL, qmax, 0) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(FULL, qmax, o));
+        bad = __any_sync(FULL, bad);
+        const double bx = isfinite(qmax) ? qmax : 0.0;
         if (lane == 0) {
             if (bad) atomicOr(a.err, ERR_NONFINITE);
             if (nt > 0) a.beta[(size_t)b * a.l + a.j] = bx;
@@ -562,8 +666,15 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
             base += __popc(mask);
         }
     } else if (a.mode == MODE_RESIDUAL) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) racc += __shfl_xor_sync(FULL, racc, o);
         if (lane == 0) a.partial[b] = racc;
     } else if (a.mode == MODE_OBJ) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) oacc[q] += __shfl_xor_sync(FULL, oacc[q], o);
+        }
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) a.part4[(size_t)b * 4 + q] = oacc[q];
@@ -595,30 +706,45 @@ __global__ void __launch_bounds__(32) k_wobj(SweepArgs a)
     extern __shared__ __align__(16) unsigned char wsm[];
     SfT<V> *Gall = reinterpret_cast<SfT<V> *>(wsm);
     __shared__ V fbuf[32][16];
+    __shared__ long long fxt[2 * NB + 1];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t t0 = a.tstart[b];
     const int n = (int)(a.tstart[b + 1] - t0);
     double beta[NB];
-    warp_betas(a, b, a.j, NB, beta);
+    warp_betas<NB>(a, b, a.j, beta);
     double sb = 0.0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) sb += beta[k];
 
     R rb;
     rb.init(a, b);
+    rb.setup_fx(beta, fxt);
     R rf;
     rf.init(a, b);
+    rf.fx = fxt;
     rf.load_carries(sfp<V>(a.fcarry), b, beta, NB + 1);
     // exp(gamma^F_s + gamma^G_{l-s} - w_s span) = mu_s 2^(n_s), by lane s
     int en = 0;
     V em = V(0);
     if (lane <= NB) {
         const int s = lane;
-        const double c = (rf.gam_at(s) + rb.gam_at(NB - s) - (double)R::rate(s) * (double)rf.span) * kLog2e;
-        const double fl = floor(c);
-        en = (int)fl;
-        em = vexp2<V>((V)(c - fl));
+        if constexpr (sizeof(V) == 4) {
+            long long g1 = 0, g2 = 0;
+#pragma unroll
+            for (int q = 0; q <= NB; ++q) {
+                if (q == s) g1 = fxt[NB + q];
+                if (q == NB - s) g2 = fxt[NB + q];
+            }
+            const long long X = g1 + g2 - fx_log2((double)R::rate(s) * (double)rf.span);
+            en = (int)(X >> 32);
+            em = exp2f((float)(unsigned)(X & 0xffffffffll) * 2.3283064365386963e-10f);
+        } else {
+            const double c = (rf.gam_at(s) + rb.gam_at(NB - s) - (double)R::rate(s) * (double)rf.span) * kLog2e;
+            const double fl = floor(c);
+            en = (int)fl;
+            em = vexp2<V>((V)(c - fl));
+        }
     }
     const bool first = (b == 0) || (a.seg && a.seg[b - 1] != a.seg[b]);
     const V gap0 = first ? V(0) : (V)(a.ulb[b] - a.urb[b - 1]);
