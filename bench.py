@@ -366,8 +366,12 @@ def run_serving(args):
             xs, mus = wl.sorted_uniform_lognormal(l=6, N=1 << 20, seed_cfg=wl.CFG_SERVING, instance=i)
         arrivals.append((float(ti), Request(rid=i, xs=xs, mus=mus, eps=eps)))
     torch.cuda.init()
+    caps = None
+    if args.autotune_cohorts:
+        from paper_2405_19246_gb300.autotune import TileCapCache
+        caps = TileCapCache(precision=args.precision, sample=16, iters=4)
     srv = Server(precision=args.precision, tol=args.tol, itr_max=args.itr_max, check_every=args.check_every,
-                 mem_budget=int(args.mem_gb * (1 << 30)))
+                 mem_budget=int(args.mem_gb * (1 << 30)), tile_caps=caps)
     t0 = time.perf_counter()
     done = srv.run(arrivals)
     wall = time.perf_counter() - t0
@@ -387,7 +391,8 @@ def run_serving(args):
                                    "batched configuration plus 1%% large (l=6, N=2^20); stop at residual "
                                    "%.0e or %d iterations" % (args.rate, args.duration, args.tol, args.itr_max),
                        "requests": n, "rate": args.rate, "mem_budget_gb": args.mem_gb,
-                       "check_every": args.check_every, "cohorts": srv.admissions},
+                       "check_every": args.check_every, "cohorts": srv.admissions,
+                       "tile_caps": {str(k): v for k, v in caps.table.items()} if caps else "kernel maximum"},
             "latency": st,
             "fp64_one_at_a_time": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                                    "solves_per_s": n / clock if clock > 0 else None,
@@ -413,6 +418,8 @@ def main():
     ap.add_argument("--mem-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune-cohorts", action="store_true",
+                    help="serving: tune the tile cap per (l, N, eps) bucket of the cohorts")
     args = ap.parse_args()
     if args.workload == "batched" and args.impl == "ours":
         return run_batched(args)

@@ -96,6 +96,15 @@ __device__ __forceinline__ float f2_exp(F2 x)
     return exp2f(y) * fmaf(ye, 0.69314718f, 1.0f);
 }
 
+// 1/x rounded to nearest (the same value as V(1) / x, without the general
+// division sequence)
+template <typename V>
+__device__ __forceinline__ V vrcp(V x);
+template <>
+__device__ __forceinline__ float vrcp<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double vrcp<double>(double x) { return __drcp_rn(x); }
+
 // 2^d as V for an integer d (0 below the normal range, the largest finite
 // power of two above it)
 template <typename V>
@@ -387,7 +396,7 @@ struct TileRun {
 #pragma unroll
                 for (int e = 0; e < PV; ++e) {
                     sp->ppe[(q * PV + e) * NT + tid] = pu[e];
-                    sp->ppm[(q * PV + e) * NT + tid] = V(1) / pu[e];
+                    sp->ppm[(q * PV + e) * NT + tid] = vrcp<V>(pu[e]);
                     sp->pph[(q * PV + e) * NT + tid] = pv[e];
                 }
             }
@@ -1057,7 +1066,7 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
             // e^{-(2s - NB) pos} = pe^{NB - 2s}
             V q[NB + 1];
             {
-                const V p1 = sm.tpe[sl], m1 = V(1) / p1;
+                const V p1 = sm.tpe[sl], m1 = vrcp<V>(p1);
                 static_for<0, NB + 1>([&](auto sc) {
                     constexpr int s = decltype(sc)::value;
                     constexpr int e = NB - 2 * s;

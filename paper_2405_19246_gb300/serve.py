@@ -127,7 +127,7 @@ class Server:
 
     def __init__(self, precision="fp32", tol=1e-6, itr_max=10000, check_every=20,
                  mem_budget=64 << 30, max_cohort=4096, keep_potentials=False, make_batch=None,
-                 tick=0.002):
+                 tick=0.002, tile_caps=None):
         self.precision = precision
         self.tol = tol
         self.itr_max = itr_max
@@ -137,6 +137,9 @@ class Server:
         self.keep_potentials = keep_potentials
         self.tick = tick
         self.make_batch = make_batch or self._default_batch
+        # optional autotune.TileCapCache: cohorts of a known (l, N, eps)
+        # bucket reuse its tuned cap on the points per tile
+        self.tile_caps = tile_caps
         self.waiting = collections.deque()
         self.cohorts: List[Cohort] = []
         self.finished: List[Request] = []
@@ -148,7 +151,9 @@ class Server:
         import torch
         from .api import Batch
         stream = torch.cuda.Stream()
-        return Batch([(r.xs, r.mus, r.eps) for r in reqs], precision=self.precision, stream=stream)
+        inst = [(r.xs, r.mus, r.eps) for r in reqs]
+        tp = self.tile_caps.cap(inst) if self.tile_caps is not None else 0
+        return Batch(inst, precision=self.precision, stream=stream, tile_points=tp)
 
     def submit(self, req: Request, now: Optional[float] = None):
         req.arrival = time.perf_counter() if now is None else now

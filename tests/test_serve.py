@@ -98,3 +98,24 @@ def test_oversized_request_runs_alone():
     srv = Server(check_every=10, mem_budget=1, make_batch=lambda rs: FakeBatch(rs, need))
     done = srv.run([(0.0, r) for r in reqs])
     assert len(done) == 3 and FakeBatch.peak == 1
+
+
+def test_tile_cap_cache_tunes_each_bucket_once():
+    from paper_2405_19246_gb300.autotune import TileCapCache, bucket_key
+    calls = []
+
+    def tuner(inst):
+        calls.append(len(inst))
+        return 512, {0: 2.0, 512: 1.0}
+
+    def inst(l, N, eps):
+        return ([np.zeros(N)] * l, [np.full(N, 1.0 / N)] * l, eps)
+
+    cache = TileCapCache(tuner=tuner)
+    a = [inst(4, 1000, 1e-2), inst(4, 1100, 1.2e-2), inst(3, 900, 1e-2)]
+    b = [inst(4, 1050, 1.1e-2), inst(4, 1000, 1e-2)]
+    c = [inst(4, 1000, 1e-3)]
+    assert bucket_key(a) == (4, 10, -4) and bucket_key(b) == bucket_key(a)
+    assert bucket_key(c) != bucket_key(a)
+    assert cache.cap(a) == 512 and cache.cap(b) == 512 and calls == [3]
+    assert cache.cap(c) == 512 and calls == [3, 1]
