@@ -798,6 +798,74 @@ mmot_status read_scalar(mmot_plan p, const double *d, double *h)
 }
 
 // Re-centre the merged-order copy of ln phi_k after g_k changed on the host side.
+// flag[0] |= 1 if some g[i] is NaN or +inf
+__global__ void k_check_pot(const double *g, int64_t n, int *flag)
+{
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = g[i];
+        if (v != v || v == INFINITY) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// New potentials g_k (device) into the stream copies of phi_k: per tile the
+// baseline beta = max of g/eps over the tile's points of marginal k (0 if
+// none is finite), then ln phi - beta and (tile kernels) e^{g/eps - beta} at
+// those points.  One block per tile; the tile's points of marginal k are
+// ranked in merged order (local index = points of k before the tile + rank).
+template <typename Tv>
+__global__ void __launch_bounds__(256) k_recentre(const uint32_t *tstart, const uint8_t *mid, const int32_t *cnt,
+                                                  const uint32_t *toff, int l, int k, double inv_eps,
+                                                  const double *g, double *beta, Tv *lphi, Tv *ephi)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int b = blockIdx.x;
+    const uint32_t t0 = tstart[b];
+    const int n = (int)(tstart[b + 1] - t0);
+    const int32_t off = cnt[(size_t)b * l + k];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    __shared__ int s_cnt[8];
+    __shared__ double s_max[8];
+    // rank of the point r among the tile's points of k, -1 if not of k
+    auto walk = [&](auto &&fn) {
+        int base = 0;
+        for (int c0 = 0; c0 < n; c0 += 256) {
+            const int r = c0 + tid;
+            const bool hit = r < n && mid[t0 + r] == k;
+            const unsigned bal = __ballot_sync(FULL, hit);
+            __syncthreads();
+            if (lane == 0) s_cnt[w] = __popc(bal);
+            __syncthreads();
+            int before = 0, tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = s_cnt[q];
+                if (q < w) before += c;
+                tot += c;
+            }
+            if (hit) fn(r, base + before + __popc(bal & ((1u << lane) - 1u)));
+            base += tot;
+        }
+    };
+    double mx = -INFINITY;
+    walk([&](int, int rank) { mx = fmax(mx, g[off + rank] * inv_eps); });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+    if (lane == 0) s_max[w] = mx;
+    __syncthreads();
+    double bx = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bx = fmax(bx, s_max[q]);
+    if (!(bx > -INFINITY && bx < INFINITY)) bx = 0.0;
+    if (tid == 0) beta[(size_t)b * l + k] = bx;
+    walk([&](int r, int rank) {
+        const double v = g[off + rank] * inv_eps - bx;
+        lphi[t0 + r] = (Tv)v;
+        if (ephi) ephi[toff[b] + r] = (v == -INFINITY) ? Tv(0) : (Tv)exp(v);
+    });
+}
+
 mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
 {
     const int l = p->l;
@@ -1405,12 +1473,45 @@ mmot_status mmot_set_potentials(mmot_plan p, int k, const double *g_in)
 {
     if (!p || !g_in) return fail(MMOT_ERR_INVALID_ARG, "NULL plan or input");
     if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
-    std::vector<double> g(p->N[k]);
-    CUDA_TRY(cudaMemcpy(g.data(), g_in, sizeof(double) * p->N[k], cudaMemcpyDefault));
-    for (int64_t i = 0; i < p->N[k]; ++i)
-        if (std::isnan(g[i]) || g[i] == INFINITY)
-            return fail(MMOT_ERR_INVALID_ARG, "g[%lld] is NaN or +inf", (long long)i);
-    return upload_potential(p, k, g);
+    if (p->batch) {
+        std::vector<double> g(p->N[k]);
+        CUDA_TRY(cudaMemcpy(g.data(), g_in, sizeof(double) * p->N[k], cudaMemcpyDefault));
+        for (int64_t i = 0; i < p->N[k]; ++i)
+            if (std::isnan(g[i]) || g[i] == INFINITY)
+                return fail(MMOT_ERR_INVALID_ARG, "g[%lld] is NaN or +inf", (long long)i);
+        return upload_potential(p, k, g);
+    }
+    // on the device: the input into the plan's scratch (device input: after
+    // all work queued on the device), a check for NaN / +inf (one flag read
+    // back), then the copy into g_k and the re-centred stream copies
+    const size_t nb = sizeof(double) * p->N[k];
+    if (is_device_ptr(g_in)) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaMemcpyAsync(p->scratch, g_in, nb, cudaMemcpyDeviceToDevice, p->st));
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(p->scratch, g_in, nb, cudaMemcpyHostToDevice, p->st));
+    }
+    CUDA_TRY(cudaMemsetAsync(p->cflags, 0, sizeof(int), p->st));
+    k_check_pot<<<64, 256, 0, p->st>>>(p->scratch, p->N[k], p->cflags);
+    CUDA_TRY(cudaGetLastError());
+    int bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, p->cflags, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    if (bad) return fail(MMOT_ERR_INVALID_ARG, "g contains NaN or +inf");
+    CUDA_TRY(cudaMemcpyAsync(p->g[k], p->scratch, nb, cudaMemcpyDeviceToDevice, p->st));
+    if (p->esz == 8)
+        k_recentre<double><<<p->nt, 256, 0, p->st>>>(p->tstart, p->mid, p->cnt, p->toff, p->l, k, 1.0 / p->eps,
+                                                     p->g[k], p->beta, static_cast<double *>(p->lphi),
+                                                     p->three_phase ? static_cast<double *>(p->ephi) : nullptr);
+    else
+        k_recentre<float><<<p->nt, 256, 0, p->st>>>(p->tstart, p->mid, p->cnt, p->toff, p->l, k, 1.0 / p->eps,
+                                                    p->g[k], p->beta, static_cast<float *>(p->lphi),
+                                                    p->three_phase ? static_cast<float *>(p->ephi) : nullptr);
+    CUDA_TRY(cudaGetLastError());
+    p->launches += 3;
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    p->ops_target = -1;
+    return MMOT_OK;
 }
 
 mmot_status mmot_set_option(mmot_plan p, int option, int64_t value)

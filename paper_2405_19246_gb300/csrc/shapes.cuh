@@ -55,7 +55,7 @@ struct WShape {
 // Lanes per tile and points per lane of the tile kernels of l <= 5
 // (tile.cuh), NT * C = Shape<NB, V>::K.  JCAP: the most points of one
 // marginal a tile may hold (the tiling cuts a tile earlier otherwise): the
-// share 1/l of a tile plus 1/16 of the tile, a multiple of 32; the tile
+// share 1/l of a tile plus 32, a multiple of 32; the tile
 // kernels keep the forward and backward states of every target point in
 // shared memory, so the bound sets their shared memory.
 template <int NB, typename V>
@@ -63,7 +63,7 @@ struct TShape {
     static constexpr int C = (sizeof(V) == 4) ? 16 : 8;
     static constexpr int K = Shape<NB, V>::K;
     static constexpr int NT = K / C;
-    static constexpr int JCAP = ((K / (NB + 1) + K / 16) + 31) / 32 * 32;
+    static constexpr int JCAP = ((K / (NB + 1) + 32) + 31) / 32 * 32;
     static_assert(NT % 32 == 0 && NT * C == K, "tile of whole warps");
 };
 

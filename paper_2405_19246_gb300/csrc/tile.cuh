@@ -261,11 +261,12 @@ __host__ __device__ constexpr int op_index(int s, int U)
     return -1;
 }
 
-// resident blocks per SM the register allocation is sized for (FP32: three
-// 128-thread or two 256-thread tiles; FP64: the registers it needs)
+// resident blocks per SM the register allocation is sized for (FP32: four
+// tiles of up to 128 threads, whose shared memory also fits four to an SM, or
+// two 256-thread tiles; FP64: the registers it needs)
 template <typename V, int NT>
 struct TileMinBlocks {
-    static constexpr int value = (sizeof(V) == 4) ? (NT >= 256 ? 2 : 3) : 1;
+    static constexpr int value = (sizeof(V) == 4) ? (NT >= 256 ? 2 : 4) : 1;
 };
 
 template <int NB, typename V, int NT, int C, int JCAP>
@@ -302,7 +303,6 @@ struct TileSm {
     // does not fit the instruction cache)
     alignas(16) V pph[C * NT];   // scaled phi
     V ppe[C * NT];               // e^{pos}
-    V ppm[C * NT];               // e^{-pos} (one division per point and kernel)
     uint8_t pmd[C * NT];         // marginal (0xff: padding)
     __device__ V *gst() { return area; }
     __device__ V *fst() { return area + GSZ; }
@@ -335,7 +335,6 @@ struct TileRun {
 
     __device__ __forceinline__ V ph(int c) const { return sp->pph[c * NT + tid]; }
     __device__ __forceinline__ V pe(int c) const { return sp->ppe[c * NT + tid]; }
-    __device__ __forceinline__ V pm(int c) const { return sp->ppm[c * NT + tid]; }
     __device__ __forceinline__ void set_ph(int c, V v) { sp->pph[c * NT + tid] = v; }
     __device__ __forceinline__ int mid_of(int c) const { return sp->pmd[c * NT + tid]; }
     __device__ __forceinline__ static int bit_of(int m, int j) { return (m == 0xff) ? -2 : (m == j ? -1 : (m < j ? m : m - 1)); }
@@ -396,7 +395,6 @@ struct TileRun {
 #pragma unroll
                 for (int e = 0; e < PV; ++e) {
                     sp->ppe[(q * PV + e) * NT + tid] = pu[e];
-                    sp->ppm[(q * PV + e) * NT + tid] = vrcp<V>(pu[e]);
                     sp->pph[(q * PV + e) * NT + tid] = pv[e];
                 }
             }
@@ -410,7 +408,6 @@ struct TileRun {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 sp->ppe[c * NT + tid] = V(1);
-                sp->ppm[c * NT + tid] = V(1);
                 sp->pph[c * NT + tid] = V(0);
                 sp->pmd[c * NT + tid] = 0xff;
             }
@@ -424,7 +421,7 @@ struct TileRun {
     __device__ __forceinline__ void facs(int c, const PassC<NB, V> &P, V (&f)[NB + 1]) const
     {
         const V pc = pe(c);
-        const V pinv = pm(c);
+        const V pinv = vrcp<V>(pc);
         const V up = FWD ? pc : pinv;
         const V dn = FWD ? pinv : pc;
         const V up2 = up * up, dn2 = dn * dn;

@@ -116,3 +116,38 @@ def test_memory_limit_gives_oom(Plan):
         plan.close()
     finally:
         L.mmot_set_memory_limit(0)
+
+
+def test_set_potentials_rejects_nan_and_keeps_the_plan(Plan):
+    """mmot_set_potentials checks its input on the device before it changes
+    anything: a NaN or +inf is MMOT_ERR_INVALID_ARG and the plan keeps its
+    potentials; host and device inputs then give the oracle's products."""
+    import torch
+    from paper_2405_19246_gb300 import _native as nat
+    l, N, eps = 4, 3000, 1e-2
+    xs, mus = wl.sorted_uniform_lognormal(l=l, N=N, instance=95)
+    rng = np.random.default_rng(95)
+    gs = [-eps * math.log(N) + 0.5 * eps * rng.standard_normal(N) for _ in range(l)]
+    gs[2][::7] = -np.inf   # zero scalings are allowed
+    plan = Plan(xs, mus, eps, precision="fp32")
+    for k in range(l):
+        if k % 2:
+            plan.set_potentials(k, torch.from_numpy(gs[k]).cuda())
+        else:
+            plan.set_potentials(k, gs[k])
+    before = [plan.get_potentials(k) for k in range(l)]
+    for bad in (np.nan, np.inf):
+        g = gs[1].copy()
+        g[N // 2] = bad
+        with pytest.raises(nat.MmotError) as ei:
+            plan.set_potentials(1, g)
+        assert ei.value.status == 1   # MMOT_ERR_INVALID_ARG
+    for k in range(l):
+        assert np.array_equal(plan.get_potentials(k), before[k])
+    for j in range(l):
+        ref = oracle.marginal_subset(xs, gs, eps, j)
+        got = plan.marginal(j, "lnM")
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(got), fin)
+        assert float(np.max(np.abs(got[fin] - ref[fin]))) <= 1e-5, j
+    plan.close()
