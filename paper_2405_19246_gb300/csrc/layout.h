@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "mmot_internal.cuh"
@@ -34,6 +35,29 @@ struct HostLayout {
     std::vector<int32_t> reftile;            // [nt*l] nearest tile holding points of m
 };
 
+// f(part) for part = 0..parts-1 on up to `parts` host threads
+template <typename F>
+inline void host_parallel(int parts, F &&f)
+{
+    if (parts <= 1) {
+        f(0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(parts - 1);
+    for (int p = 1; p < parts; ++p) th.emplace_back([&f, p] { f(p); });
+    f(0);
+    for (auto &t : th) t.join();
+}
+
+// host threads for a layout of T points (one below a million points)
+inline int layout_threads(int64_t T)
+{
+    if (T < (1 << 20)) return 1;
+    const unsigned hc = std::thread::hardware_concurrency();
+    return (int)std::min<unsigned>(16u, std::max(1u, hc));
+}
+
 inline void build_layout(int l, const int64_t *N, const std::vector<std::vector<double>> &hx, double eps,
                          int K, int jcap, double limit, HostLayout &L)
 {
@@ -45,18 +69,39 @@ inline void build_layout(int l, const int64_t *N, const std::vector<std::vector<
     L.mid.resize(T);
     for (int k = 0; k < l; ++k) L.mpos[k].resize(N[k]);
     {
-        std::vector<int64_t> head(l, 0);
-        for (int64_t t = 0; t < T; ++t) {
-            int best = -1;
-            for (int k = 0; k < l; ++k) {
-                if (head[k] >= N[k]) continue;
-                if (best < 0 || hx[k][head[k]] < hx[best][head[best]]) best = k;
-            }
-            L.xm[t] = hx[best][head[best]];
-            L.mid[t] = (uint8_t)best;
-            L.mpos[best][head[best]] = (uint32_t)t;
-            head[best] += 1;
+        // The merge in P independent parts: part p takes, of every marginal,
+        // the points with x in [v_p, v_{p+1}) (split values from the largest
+        // marginal), so equal coordinates never straddle two parts and each
+        // part's merged offset is the number of points below v_p.
+        const int P = layout_threads(T);
+        int kbig = 0;
+        for (int k = 1; k < l; ++k)
+            if (N[k] > N[kbig]) kbig = k;
+        std::vector<std::vector<int64_t>> lo(P + 1, std::vector<int64_t>(l, 0));
+        for (int k = 0; k < l; ++k) lo[P][k] = N[k];
+        for (int p = 1; p < P; ++p) {
+            const double v = hx[kbig][(size_t)(N[kbig] * p / P)];
+            for (int k = 0; k < l; ++k)
+                lo[p][k] = std::lower_bound(hx[k].begin(), hx[k].end(), v) - hx[k].begin();
         }
+        host_parallel(P, [&](int p) {
+            std::vector<int64_t> head(lo[p]);
+            int64_t t = 0;
+            for (int k = 0; k < l; ++k) t += lo[p][k];
+            int64_t tend = 0;
+            for (int k = 0; k < l; ++k) tend += lo[p + 1][k];
+            for (; t < tend; ++t) {
+                int best = -1;
+                for (int k = 0; k < l; ++k) {
+                    if (head[k] >= lo[p + 1][k]) continue;
+                    if (best < 0 || hx[k][head[k]] < hx[best][head[best]]) best = k;
+                }
+                L.xm[t] = hx[best][head[best]];
+                L.mid[t] = (uint8_t)best;
+                L.mpos[best][head[best]] = (uint32_t)t;
+                head[best] += 1;
+            }
+        });
     }
     double wmax = 0.0;
     for (int s = 0; s <= l; ++s) wmax = std::max(wmax, (double)s * (l - s));
@@ -89,20 +134,32 @@ inline void build_layout(int l, const int64_t *N, const std::vector<std::vector<
     L.pos.resize(T);
     L.cnt.assign((size_t)nt * l, 0);
     L.reftile.assign((size_t)nt * l, -1);
-    std::vector<int32_t> run(l, 0);
-    for (int b = 0; b < nt; ++b) {
-        L.xlb[b] = L.xm[L.tstart[b]];
-        L.xrb[b] = L.xm[L.tstart[b + 1] - 1];
-        L.ulb[b] = L.xlb[b] / eps;
-        L.urb[b] = L.xrb[b] / eps;
-        L.span[b] = (L.xrb[b] - L.xlb[b]) / eps;
-        for (int k = 0; k < l; ++k) L.cnt[(size_t)b * l + k] = run[k];
-        for (uint32_t t = L.tstart[b]; t < L.tstart[b + 1]; ++t) {
-            L.pos[t] = (L.xm[t] - L.xlb[b]) / eps;
-            L.tile_of[t] = (uint32_t)b;
-            run[L.mid[t]] += 1;
-            L.reftile[(size_t)b * l + L.mid[t]] = b;
-        }
+    {
+        // per tile (in parallel): ends, positions, tile of each point and the
+        // tile's points per marginal; then the counts before each tile
+        const int P = layout_threads(T);
+        host_parallel(P, [&](int p) {
+            for (int b = (int)((int64_t)nt * p / P); b < (int)((int64_t)nt * (p + 1) / P); ++b) {
+                L.xlb[b] = L.xm[L.tstart[b]];
+                L.xrb[b] = L.xm[L.tstart[b + 1] - 1];
+                L.ulb[b] = L.xlb[b] / eps;
+                L.urb[b] = L.xrb[b] / eps;
+                L.span[b] = (L.xrb[b] - L.xlb[b]) / eps;
+                for (uint32_t t = L.tstart[b]; t < L.tstart[b + 1]; ++t) {
+                    L.pos[t] = (L.xm[t] - L.xlb[b]) / eps;
+                    L.tile_of[t] = (uint32_t)b;
+                    L.cnt[(size_t)b * l + L.mid[t]] += 1;
+                    L.reftile[(size_t)b * l + L.mid[t]] = b;
+                }
+            }
+        });
+        std::vector<int32_t> run(l, 0);
+        for (int b = 0; b < nt; ++b)
+            for (int k = 0; k < l; ++k) {
+                const int32_t c = L.cnt[(size_t)b * l + k];
+                L.cnt[(size_t)b * l + k] = run[k];
+                run[k] += c;
+            }
     }
     // tiles without points of marginal m use the nearest earlier tile that has
     // some, else the nearest later one

@@ -1201,7 +1201,15 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
             for (int64_t i = seg_off[(size_t)q * l + k]; i < seg_off[(size_t)(q + 1) * l + k]; ++i) hg[k][i] = g0;
         }
         hlm[k].resize(N[k]);
-        for (int64_t i = 0; i < N[k]; ++i) hlm[k][i] = hmu[k][i] > 0 ? std::log(hmu[k][i]) : -INFINITY;
+        {
+            const int P = layout_threads(N[k]);
+            const int64_t n = N[k];
+            std::vector<double> &dst = hlm[k];
+            const std::vector<double> &src = hmu[k];
+            host_parallel(P, [&](int pp) {
+                for (int64_t i = n * pp / P; i < n * (pp + 1) / P; ++i) dst[i] = src[i] > 0 ? std::log(src[i]) : -INFINITY;
+            });
+        }
         ce = up(p->g[k], hg[k].data(), sizeof(double) * N[k]);
         ce = ce ? ce : up(p->lnmu[k], hlm[k].data(), sizeof(double) * N[k]);
         ce = ce ? ce : up(p->mu[k], hmu[k].data(), sizeof(double) * N[k]);
@@ -1222,29 +1230,35 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         const size_t Tp = (size_t)p->Tpad;
         std::vector<unsigned char> hep(Tp * p->esz), hph(Tp * p->esz);
         std::vector<uint8_t> hem(Tp, 0xff);
-        for (size_t u = 0; u < Tp; ++u) {
-            if (fp64) {
-                reinterpret_cast<double *>(hep.data())[u] = 1.0;
-                reinterpret_cast<double *>(hph.data())[u] = 0.0;
-            } else {
-                reinterpret_cast<float *>(hep.data())[u] = 1.0f;
-                reinterpret_cast<float *>(hph.data())[u] = 0.0f;
-            }
-        }
-        for (int b = 0; b < nt; ++b) {
-            for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
-                const size_t u = (size_t)p->h_toff[b] + (t - ts[b]);
-                const double e = std::exp(hpos[t]);
-                if (fp64) {
-                    reinterpret_cast<double *>(hep.data())[u] = e;
-                    reinterpret_cast<double *>(hph.data())[u] = 1.0;
-                } else {
-                    reinterpret_cast<float *>(hep.data())[u] = (float)e;
-                    reinterpret_cast<float *>(hph.data())[u] = 1.0f;
+        // by tile, in parallel: the tile's padded range [toff[b], toff[b+1])
+        // (the last one to Tp) with padding values, then its points
+        const int P = layout_threads((int64_t)Tp);
+        host_parallel(P, [&](int pp) {
+            for (int b = (int)((int64_t)nt * pp / P); b < (int)((int64_t)nt * (pp + 1) / P); ++b) {
+                const size_t u0 = p->h_toff[b], u1 = (b + 1 < nt) ? p->h_toff[b + 1] : Tp;
+                for (size_t u = u0; u < u1; ++u) {
+                    if (fp64) {
+                        reinterpret_cast<double *>(hep.data())[u] = 1.0;
+                        reinterpret_cast<double *>(hph.data())[u] = 0.0;
+                    } else {
+                        reinterpret_cast<float *>(hep.data())[u] = 1.0f;
+                        reinterpret_cast<float *>(hph.data())[u] = 0.0f;
+                    }
                 }
-                hem[u] = p->h_mid[t];
+                for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
+                    const size_t u = (size_t)p->h_toff[b] + (t - ts[b]);
+                    const double e = std::exp(hpos[t]);
+                    if (fp64) {
+                        reinterpret_cast<double *>(hep.data())[u] = e;
+                        reinterpret_cast<double *>(hph.data())[u] = 1.0;
+                    } else {
+                        reinterpret_cast<float *>(hep.data())[u] = (float)e;
+                        reinterpret_cast<float *>(hph.data())[u] = 1.0f;
+                    }
+                    hem[u] = p->h_mid[t];
+                }
             }
-        }
+        });
         ce = ce ? ce : up(p->toff, p->h_toff.data(), sizeof(uint32_t) * nt);
         ce = ce ? ce : up(p->epos, hep.data(), hep.size());
         ce = ce ? ce : up(p->ephi, hph.data(), hph.size());
