@@ -164,6 +164,9 @@ typedef struct {
     int precision;
     int64_t kernel_launches;   /* library kernels launched on this plan so far */
     int64_t device_bytes;      /* device memory held by the plan */
+    int uniform_grid;          /* 1: every marginal on one uniform grid, l <= 5 (Sec. 3's
+                                  setting): the tile kernels form each point's position factor
+                                  and marginal from its merged index instead of reading them */
 } mmot_plan_info;
 mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info);
 

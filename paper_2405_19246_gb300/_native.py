@@ -47,7 +47,8 @@ class MmotPlanInfo(ctypes.Structure):
     _fields_ = [("total_points", ctypes.c_int64), ("tiles", ctypes.c_int64),
                 ("tile_points", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("launches_per_iteration", ctypes.c_int), ("precision", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("uniform_grid", ctypes.c_int)]
 
 
 class MmotBatchInfo(ctypes.Structure):

@@ -197,6 +197,7 @@ struct mmot_plan_s {
     unsigned char *pdecF = nullptr, *pdecB = nullptr;
     unsigned char *coef = nullptr;   // level passes (l >= 6): per tile and marginal, level-to-level coefficients
     void *lops = nullptr;            // tile kernels (l <= 5): lanes' chunk operators of the current target
+    void *ugrid = nullptr;           // uniform grid: e^{d h / eps} by grid steps d (no epos / emid)
     int *cflags = nullptr;          // carry-scan chunk flags
     size_t cflags_n = 0;
     unsigned char *cagg = nullptr;  // carry-scan chunk contributions [2][32][NS]
@@ -458,6 +459,7 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.frozen = p->d_frozen;
     a.inflow = (p->shard && j < p->l && p->inflow_target == j) ? p->inflow : nullptr;
     a.lops = (j < p->l) ? p->lops : nullptr;
+    a.ugrid = p->ugrid;
     a.shard_end = (p->shard && j < p->l) ? 1 : 0;
     return a;
 }
@@ -966,6 +968,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     }
     if (tile_points > 0) K = std::max(32, std::min(K, tile_points));
     const double limit = fp64 ? kSpanLimitF64 : kSpanLimitF32;
+    double ugrid_h = 0.0;   // > 0: one uniform grid of step ugrid_h for every marginal
     HostLayout L;
     L.l = l;
     std::vector<std::vector<double>> hmu(l);
@@ -1001,6 +1004,21 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
                 return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, (double)sum);
             hmu[k].insert(hmu[k].end(), qmu[k].begin(), qmu[k].end());
             seg_off[(size_t)(q + 1) * l + k] = seg_off[(size_t)q * l + k] + n;
+        }
+        if (nin == 1) {
+            // one uniform grid for every marginal: identical coordinates,
+            // x_i = x_0 + i h within 1e-9 h (tile kernels, l <= 5)
+            bool u = (l - 1 <= kMaxOpBits) && in.N[0] >= 2;
+            for (int k = 1; k < l && u; ++k) u = (in.N[k] == in.N[0]) && (hx[k] == hx[0]);
+            double h = 0.0;
+            if (u) {
+                const int64_t n = in.N[0];
+                h = (hx[0][n - 1] - hx[0][0]) / (double)(n - 1);
+                u = h > 0.0;
+                for (int64_t i = 0; i < n && u; ++i)
+                    u = std::fabs(hx[0][i] - (hx[0][0] + (double)i * h)) <= 1e-9 * h;
+            }
+            ugrid_h = u ? h : 0.0;
         }
         HostLayout Lq;
         build_layout(l, in.N, hx, in.eps, K, jcap, limit, Lq);
@@ -1136,11 +1154,16 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         }
         PA(p->toff, nt);
         unsigned char *q1 = nullptr, *q2 = nullptr;
-        PA(q1, (size_t)p->Tpad * p->esz);
+        if (ugrid_h > 0.0) {
+            PA(q1, (size_t)(K / l + 2) * p->esz);   // grid steps within one tile
+            p->ugrid = q1;
+        } else {
+            PA(q1, (size_t)p->Tpad * p->esz);
+            p->epos = q1;
+            PA(p->emid, p->Tpad);
+        }
         PA(q2, (size_t)p->Tpad * p->esz);
-        p->epos = q1;
         p->ephi = q2;
-        PA(p->emid, p->Tpad);
         if (!fp64)
             for (int k = 0; k < l; ++k) PA(p->lnmu_ff[k], N[k]);
     }
@@ -1228,8 +1251,9 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     if (p->three_phase) {
         // padded stream: e^{pos}, scaled phi (1: lphi = 0), marginal (0xff: padding)
         const size_t Tp = (size_t)p->Tpad;
-        std::vector<unsigned char> hep(Tp * p->esz), hph(Tp * p->esz);
-        std::vector<uint8_t> hem(Tp, 0xff);
+        const bool ug = (p->ugrid != nullptr);
+        std::vector<unsigned char> hep(ug ? 0 : Tp * p->esz), hph(Tp * p->esz);
+        std::vector<uint8_t> hem(ug ? 0 : Tp, 0xff);
         // by tile, in parallel: the tile's padded range [toff[b], toff[b+1])
         // (the last one to Tp) with padding values, then its points
         const int P = layout_threads((int64_t)Tp);
@@ -1238,31 +1262,48 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
                 const size_t u0 = p->h_toff[b], u1 = (b + 1 < nt) ? p->h_toff[b + 1] : Tp;
                 for (size_t u = u0; u < u1; ++u) {
                     if (fp64) {
-                        reinterpret_cast<double *>(hep.data())[u] = 1.0;
+                        if (!ug) reinterpret_cast<double *>(hep.data())[u] = 1.0;
                         reinterpret_cast<double *>(hph.data())[u] = 0.0;
                     } else {
-                        reinterpret_cast<float *>(hep.data())[u] = 1.0f;
+                        if (!ug) reinterpret_cast<float *>(hep.data())[u] = 1.0f;
                         reinterpret_cast<float *>(hph.data())[u] = 0.0f;
                     }
                 }
                 for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
                     const size_t u = (size_t)p->h_toff[b] + (t - ts[b]);
-                    const double e = std::exp(hpos[t]);
-                    if (fp64) {
-                        reinterpret_cast<double *>(hep.data())[u] = e;
+                    if (fp64)
                         reinterpret_cast<double *>(hph.data())[u] = 1.0;
-                    } else {
-                        reinterpret_cast<float *>(hep.data())[u] = (float)e;
+                    else
                         reinterpret_cast<float *>(hph.data())[u] = 1.0f;
-                    }
+                    if (ug) continue;
+                    const double e = std::exp(hpos[t]);
+                    if (fp64)
+                        reinterpret_cast<double *>(hep.data())[u] = e;
+                    else
+                        reinterpret_cast<float *>(hep.data())[u] = (float)e;
                     hem[u] = p->h_mid[t];
                 }
             }
         });
         ce = ce ? ce : up(p->toff, p->h_toff.data(), sizeof(uint32_t) * nt);
-        ce = ce ? ce : up(p->epos, hep.data(), hep.size());
+        std::vector<unsigned char> hug;
+        if (ug) {
+            // e^{d h / eps}, d = 0 .. K / l + 1 grid steps
+            const int nd = K / l + 2;
+            hug.resize((size_t)nd * p->esz);
+            for (int d = 0; d < nd; ++d) {
+                const double e = std::exp((double)d * ugrid_h / eps);
+                if (fp64)
+                    reinterpret_cast<double *>(hug.data())[d] = e;
+                else
+                    reinterpret_cast<float *>(hug.data())[d] = (float)e;
+            }
+            ce = ce ? ce : up(p->ugrid, hug.data(), hug.size());
+        } else {
+            ce = ce ? ce : up(p->epos, hep.data(), hep.size());
+            ce = ce ? ce : up(p->emid, hem.data(), hem.size());
+        }
         ce = ce ? ce : up(p->ephi, hph.data(), hph.size());
-        ce = ce ? ce : up(p->emid, hem.data(), hem.size());
         if (!fp64) {
             for (int k = 0; k < l && ce == cudaSuccess; ++k) {
                 std::vector<float2> ff(N[k]);
@@ -1626,6 +1667,7 @@ mmot_status mmot_get_info(mmot_plan p, mmot_plan_info *info)
     info->precision = p->prec;
     info->kernel_launches = p->launches;
     info->device_bytes = p->dev_bytes;
+    info->uniform_grid = (p->ugrid != nullptr) ? 1 : 0;
     return MMOT_OK;
 }
 

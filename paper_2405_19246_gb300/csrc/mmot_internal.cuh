@@ -103,6 +103,11 @@ struct SweepArgs {
     // tile kernels (l <= 5): every lane's chunk transfer operators of the
     // current target, [tile][dir][entry][lane] (null: recomputed by a walk)
     void *lops;
+    // all marginals on one uniform grid (x_i = x_0 + i h): merged point t is
+    // grid point t / l of marginal t % l, and ugrid[d] = e^{d h / eps} (V) for
+    // d grid steps from the tile's first point; epos and emid are not read
+    // (null: the general stream)
+    const void *ugrid;
     // carry scan over chunks of tiles: flags [2][G][NB+1], contributions [2][G][NS]
     int *cflags;
     void *cagg;

@@ -326,6 +326,7 @@ struct TileRun {
 
     int lane, w, tid;
     int n;            // points in the tile
+    uint32_t ts;      // merged index of the tile's first point
     int jcur;         // target whose bit mapping bt() uses
     V span;
     Sm *sp;           // the block's shared memory (per-point arrays)
@@ -384,7 +385,27 @@ struct TileRun {
         const V *ephi = static_cast<const V *>(a.ephi);
         constexpr int PV = 16 / sizeof(V);   // values per 16-byte load
         static_assert(C % PV == 0 && C % 4 == 0, "chunk of whole 16-byte pieces");
-        if (i0 < n) {
+        if (a.ugrid && i0 < n) {
+            // uniform grid: e^{pos} from the table by grid steps, the marginal
+            // from the merged index (l = NB + 1 points per grid point)
+            const V *E = static_cast<const V *>(a.ugrid);
+            const uint32_t g0 = ts / (uint32_t)L;
+#pragma unroll
+            for (int q = 0; q < C / PV; ++q) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ephi + t0 + i0) + q);
+                V pv[PV];
+                memcpy(pv, &v, 16);
+#pragma unroll
+                for (int e = 0; e < PV; ++e) {
+                    const int r = i0 + q * PV + e;
+                    const uint32_t t = ts + (uint32_t)r;
+                    const bool in = r < n;
+                    sp->ppe[(q * PV + e) * NT + tid] = in ? __ldg(E + (t / (uint32_t)L - g0)) : V(1);
+                    sp->pph[(q * PV + e) * NT + tid] = pv[e];
+                    sp->pmd[(q * PV + e) * NT + tid] = in ? (uint8_t)(t % (uint32_t)L) : (uint8_t)0xff;
+                }
+            }
+        } else if (i0 < n) {
 #pragma unroll
             for (int q = 0; q < C / PV; ++q) {
                 const uint4 u = __ldg(reinterpret_cast<const uint4 *>(epos + t0 + i0) + q);
@@ -818,6 +839,7 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tops(SweepA
     r.n = (int)(a.tstart[b + 1] - a.tstart[b]);
     r.span = (V)a.span[b];
     r.sp = &sm;
+    r.ts = a.tstart[b];
     r.load(a, a.toff[b], r.tid * C);
     tile_ops_body<NB, V, NT, C, JCAP>(r, sm, a, b, a.j);
 }
@@ -851,6 +873,7 @@ __global__ void __launch_bounds__(NT, TileMinBlocks<V, NT>::value) k_tile(SweepA
     const int l = a.l;
 
     r.sp = &sm;
+    r.ts = ts;
     r.load(a, t0, i0);
     r.set_bits(j);
     // this tile's stored lane operators of target j (forward, then backward)
