@@ -244,6 +244,26 @@ mmot_status mmot_shard_set_inflow(mmot_plan p, int k, const double *lnF, const d
 mmot_status mmot_shard_update(mmot_plan p, int k);
 mmot_status mmot_shard_residual(mmot_plan p, int k, double *res);
 
+/* ---- Two-dimensional product (Sec. 4.1, Algorithm 6, FTVP_2d) -------------
+ * Three marginals on one uniform N x M grid with steps h1 (first index) and
+ * h2 (second), L1 cost, kernel K = lambda1^{|i1-j1|+|i1-k1|+|j1-k1|}
+ * lambda2^{|i2-j2|+|i2-k2|+|j2-k2|}, lambda_d = e^{-h_d/eps}:
+ *     out(k1, k2) = sum_{i1,i2,j1,j2} K phi(i1, i2) psi(j1, j2),
+ * the product that the two-dimensional Sinkhorn iteration needs for each
+ * marginal (K is symmetric in the three marginals, so the product for the
+ * first marginal is mmot_ftvp2d(psi, varphi) and so on).  O(N M) work: the
+ * second index by the one-dimensional recurrences with vector states, each
+ * step a one-dimensional product along the first index (6 M of them, in
+ * parallel), all terms positive.
+ * phi, psi, out: N * M doubles, column-major (element (i1, i2) at i1 + N i2),
+ * host or device; FP64 in the linear domain, so inputs should be scaled to
+ * moderate values.  1 <= N, M, N M <= 2^28, 0 <= lambda_d < 1, else
+ * MMOT_ERR_INVALID_ARG.  Allocates device scratch (31 N M doubles) for the
+ * call; work on cuda_stream (NULL: the legacy default stream), synchronised
+ * before returning. */
+mmot_status mmot_ftvp2d(int64_t N, int64_t M, const double *phi, const double *psi, double lambda1,
+                        double lambda2, double *out, void *cuda_stream);
+
 /* One marginal product without any device memory allocation.
  *
  * The paper has no counterpart to this call; it serves callers that cannot

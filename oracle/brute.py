@@ -197,3 +197,24 @@ def ln_marginal_in_range(xs, gs, eps, j, lo, hi, lnF_in, lnG_in, x_L, x_R):
         m = np.max(terms)
         res.append(m + np.log(np.sum(np.exp(terms - m))) if np.isfinite(m) else -np.inf)
     return np.array(res)
+
+
+# ---- the two-dimensional product (Sec. 4.1) -----------------------------------
+
+
+def kernel_1d(n, lam):
+    """K(i, j, k) = lam^{|i-j| + |i-k| + |j-k|} on a uniform grid of n points."""
+    i = np.arange(n)
+    e = (np.abs(i[:, None, None] - i[None, :, None]) + np.abs(i[:, None, None] - i[None, None, :])
+         + np.abs(i[None, :, None] - i[None, None, :]))
+    return np.power(float(lam), e)
+
+
+def ftvp2d_dense(phi, psi, lam1, lam2):
+    """The two-dimensional product by its definition (Sec. 4.1, Eq. J_{k1k2}):
+    J(k1, k2) = sum over i1, i2, j1, j2 of K1(i1, j1, k1) K2(i2, j2, k2)
+    phi(i1, i2) psi(j1, j2), with the L1 kernel of each axis.  O(N^3 M^3)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    N, M = phi.shape
+    return np.einsum("abk,cdl,ac,bd->kl", kernel_1d(N, lam1), kernel_1d(M, lam2), phi, psi)

@@ -32,6 +32,7 @@ EXPORTED = [
     "mmot_get_potentials", "mmot_set_potentials", "mmot_reset_potentials", "mmot_set_option",
     "mmot_get_profile", "mmot_get_info", "mmot_set_memory_limit", "mmot_memory_in_use", "mmot_marginal_noalloc",
     "mmot_shard_create", "mmot_shard_operator", "mmot_shard_set_inflow", "mmot_shard_update", "mmot_shard_residual",
+    "mmot_ftvp2d",
     "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_freeze", "mmot_batch_status",
     "mmot_batch_get_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
     "mmot_destroy", "mmot_last_error",
@@ -95,6 +96,7 @@ def lib():
         L.mmot_shard_set_inflow.argtypes = [vp, i, vp, vp]
         L.mmot_shard_update.argtypes = [vp, i]
         L.mmot_shard_residual.argtypes = [vp, i, P(d)]
+        L.mmot_ftvp2d.argtypes = [i64, i64, vp, vp, d, d, vp, vp]
         L.mmot_batch_create.argtypes = [i, P(i), P(i64), P(vp), P(vp), P(d), i, i, vp, P(vp)]
         L.mmot_batch_step.argtypes = [vp, i, d, P(i)]
         L.mmot_batch_reset.argtypes = [vp]

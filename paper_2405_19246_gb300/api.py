@@ -256,3 +256,22 @@ class Batch:
         inf = nat.MmotBatchInfo()
         nat.check(nat.lib().mmot_batch_get_info(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+
+def ftvp2d(phi, psi, lambda1, lambda2):
+    """Two-dimensional product of three marginals on one uniform grid
+    (``mmot_ftvp2d``; Sec. 4.1, Algorithm 6): out = K x phi x psi for the
+    separable L1 kernel with lambda_d = exp(-h_d / eps).  phi, psi: (N, M)
+    arrays (numpy) indexed [i1, i2]; returns an (N, M) numpy array."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    if phi.shape != psi.shape or phi.ndim != 2:
+        raise ValueError("phi and psi must be (N, M) arrays of the same shape")
+    N, M = phi.shape
+    # column-major: element (i1, i2) at i1 + N i2
+    a = np.ascontiguousarray(phi.T)
+    b = np.ascontiguousarray(psi.T)
+    out = np.empty((M, N), dtype=np.float64)
+    nat.check(nat.lib().mmot_ftvp2d(N, M, a.ctypes.data, b.ctypes.data, float(lambda1), float(lambda2),
+                                    out.ctypes.data, None))
+    return out.T.copy()

@@ -264,3 +264,26 @@ def test_merge_tie_rule():
     mid, loc = oracle.merge([np.array([0.0, 1.0]), np.array([0.0, 1.0]), np.array([0.5])])
     assert list(mid) == [0, 1, 2, 0, 1]
     assert list(loc) == [0, 0, 0, 1, 1]
+
+
+# ---- the two-dimensional product (Sec. 4.1) -----------------------------------
+
+def test_ftvp2d_dense_separates_for_rank_one_inputs():
+    """For phi = a c^T and psi = b d^T the separable kernel gives
+    J = FTVP1(a, b; lam1) FTVP1(c, d; lam2)^T, each factor from the literal
+    Algorithm 2 of the C oracle (an independent code path)."""
+    from oracle import brute
+    rng = np.random.default_rng(12)
+    a, b = rng.random(6), rng.random(6)
+    c, d = rng.random(5), rng.random(5)
+    J = brute.ftvp2d_dense(np.outer(a, c), np.outer(b, d), 0.6, 0.8)
+    ref = np.outer(oracle.ftvp1(a, b, 0.6), oracle.ftvp1(c, d, 0.8))
+    assert np.max(np.abs(J - ref) / ref) < 1e-13
+
+
+def test_ftvp2d_dense_with_one_column_is_the_1d_product():
+    from oracle import brute
+    rng = np.random.default_rng(13)
+    a, b = rng.random(9), rng.random(9)
+    J = brute.ftvp2d_dense(a[:, None], b[:, None], 0.5, 0.9)
+    assert np.max(np.abs(J[:, 0] - oracle.ftvp1(a, b, 0.5)) / J[:, 0]) < 1e-13
