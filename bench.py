@@ -493,7 +493,7 @@ def main():
     target_io = w["N"] * (16 + 2 * esz)
     kbytes = {"k_fwd": stream + target_io, "k_tile": stream + target_io, "k_bwd": stream,
               "k_tops": stream, "k_carry": None, "k_wprod": stream + w["N"] * (16 + esz),
-              "k_wpass": stream, "k_lscan": None}
+              "k_wpass": stream, "k_lscan": None, "k_wbwd": stream}
     dom = max(stats, key=lambda k: stats[k][1])
     n_dom, ms_dom = stats[dom]
     avg = ms_dom / max(1, n_dom) / 1000.0
@@ -515,7 +515,7 @@ def main():
         # a forward walk plus 2^(l-1) products per target in the combine).
         # Peak: 152 SMs x 128 FP32 FMA per clock x the maximum SM clock.
         half = 1 << (w["l"] - 2)
-        fma = {"k_wpass": T * half, "k_wprod": 2 * T * half + w["N"] * (2 * half)}
+        fma = {"k_wpass": T * half, "k_wbwd": T * half, "k_wprod": T * half + w["N"] * (2 * half)}
         peak_alu = 152 * 128 * 2.07e9 / 1e12
         ach = fma[dom] / avg / 1e12 if dom in fma and avg > 0 else None
         roofline = dict(roofline, bound="alu", achieved=ach, peak=peak_alu, unit="TFMA/s",

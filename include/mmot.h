@@ -145,9 +145,10 @@ mmot_status mmot_set_option(mmot_plan p, int option, int64_t value);
  *   kernel 0: backward look-back scan (k_bwd), 1: forward look-back scan +
  *   combine (k_fwd), 2: tile transfer operators (k_tops), 3: carry scan over
  *   tiles (k_carry), 4: tile products with known carries + combine (k_tile),
- *   5: per-level tile contributions (k_lagg), 6: per-level carry scan
- *   (k_lscan).  Marginal products use kernels 2-4 for l <= 5 and 4-6 for
- *   l >= 6; kernels 0-1 serve the objective sweeps of l >= 5.
+ *   5: per-level tile contributions (k_wpass), 6: per-level carry scan
+ *   (k_lscan), 7: backward walk of the warp-tile products (k_wbwd).
+ *   Marginal products use kernels 2-4 for l <= 5 and 4-7 for l >= 6;
+ *   kernels 0-1 serve the objective sweeps of l >= 5.
  * Returns the number of launches and their summed device time in ms (CUDA
  * events on the plan's stream); synchronises the stream.  reset != 0 clears
  * the statistics after reading. */

@@ -142,12 +142,12 @@ class Plan:
         """{kernel name: (launches, total ms)} from the CUDA-event profile."""
         out = {}
         names = ((0, "k_bwd"), (1, "k_fwd"), (2, "k_tops"), (3, "k_carry"),
-                 (4, "k_tile" if self.l <= 5 else "k_wprod"), (5, "k_wpass"), (6, "k_lscan"))
+                 (4, "k_tile" if self.l <= 5 else "k_wprod"), (5, "k_wpass"), (6, "k_lscan"), (7, "k_wbwd"))
         for k, name in names:
             n = ctypes.c_int64()
             ms = ctypes.c_double()
             nat.check(nat.lib().mmot_get_profile(self._h, k, ctypes.byref(n), ctypes.byref(ms),
-                                                 1 if (reset and k == 6) else 0))
+                                                 1 if (reset and k == 7) else 0))
             out[name] = (n.value, ms.value)
         return out
 

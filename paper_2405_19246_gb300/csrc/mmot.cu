@@ -198,6 +198,7 @@ struct mmot_plan_s {
     unsigned char *coef = nullptr;   // level passes (l >= 6): per tile and marginal, level-to-level coefficients
     void *lops = nullptr;            // tile kernels (l <= 5): lanes' chunk operators of the current target
     void *ugrid = nullptr;           // uniform grid: e^{d h / eps} by grid steps d (no epos / emid)
+    void *gtarg = nullptr;           // warp tiles (l >= 6): backward states at the target points
     int *cflags = nullptr;          // carry-scan chunk flags
     size_t cflags_n = 0;
     unsigned char *cagg = nullptr;  // carry-scan chunk contributions [2][32][NS]
@@ -227,9 +228,9 @@ struct mmot_plan_s {
     int profile = 0;
     struct Rec { int kernel; cudaEvent_t a, b; };
     std::vector<Rec> recs;
-    int64_t prof_count[7] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t prof_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t launches = 0;   // kernels launched so far (graph replays included)
-    double prof_ms[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double prof_ms[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 
     ~mmot_plan_s()
     {
@@ -304,6 +305,7 @@ cudaError_t launch_lvl_nb(const SweepArgs &a, bool fp64, cudaStream_t st, int ki
         if (kind == 4) return fp64 ? launch_prod<NB, double>(a, st) : launch_prod<NB, float>(a, st);
         if (kind == 5) return fp64 ? launch_lagg<NB, double>(a, st, SL, fwd) : launch_lagg<NB, float>(a, st, SL, fwd);
         if (kind == 6) return fp64 ? launch_lscan<NB, double>(a, st, SL, fwd) : launch_lscan<NB, float>(a, st, SL, fwd);
+        if (kind == 7) return fp64 ? launch_wbwd<NB, double>(a, st) : launch_wbwd<NB, float>(a, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -460,13 +462,14 @@ SweepArgs make_args(mmot_plan p, int j, int mode, double *out)
     a.inflow = (p->shard && j < p->l && p->inflow_target == j) ? p->inflow : nullptr;
     a.lops = (j < p->l) ? p->lops : nullptr;
     a.ugrid = p->ugrid;
+    a.gtarg = p->gtarg;
     a.shard_end = (p->shard && j < p->l) ? 1 : 0;
     return a;
 }
 
 // kernels per marginal product in an iteration: carry scan + tile products
 // (three-phase, l <= 5), or 2 (NB levels x contribution + scan) + products
-int launches_per_product(mmot_plan p) { return p->three_phase ? 2 : 2 * ((p->NB + 1) / 2 + p->NB) + 1; }
+int launches_per_product(mmot_plan p) { return p->three_phase ? 2 : 2 * ((p->NB + 1) / 2 + p->NB) + 2; }
 
 // kernel ids: 2 k_tops, 3 k_carry, 4 k_tile (three-phase design, l <= 5);
 // 5 k_wpass, 6 k_lscan, 4 k_wprod (level passes and warp tiles, l >= 6);
@@ -544,6 +547,8 @@ mmot_status enqueue_product(mmot_plan p, int j, int mode, double *out, int jnext
         }
     }
     a.pair = 0;
+    mmot_status s = timed_launch(p, 7, a, fp64);
+    if (s != MMOT_OK) return s;
     return timed_launch(p, 4, a, fp64);
 }
 
@@ -1127,7 +1132,14 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     p->cflags_n = p->three_phase ? (size_t)2 * 32 * (p->NB + 1) : (size_t)2 * p->NS * 32;
     PA(p->cflags, p->cflags_n);
     PA(p->cagg, (size_t)2 * 32 * p->NS * p->sfsz);
-    if (!p->three_phase) PA(p->coef, (size_t)nt * p->NB * p->sfsz);
+    if (!p->three_phase) {
+        PA(p->coef, (size_t)nt * p->NB * p->sfsz);
+        unsigned char *gt = nullptr;
+        int64_t mx = 1;
+        for (int k = 0; k < l; ++k) mx = std::max(mx, N[k]);
+        PA(gt, (size_t)mx * p->NS * p->sfsz);
+        p->gtarg = gt;
+    }
     if (p->shard) {
         PA(p->inflow, (size_t)2 * p->NS * p->sfsz);
         PA(p->d_lnop, (size_t)2 * (p->NB + 1) * p->NS);
@@ -1634,7 +1646,7 @@ mmot_status mmot_reset_potentials(mmot_plan p)
 mmot_status mmot_get_profile(mmot_plan p, int kernel, int64_t *launches, double *total_ms, int reset)
 {
     if (!p || !launches || !total_ms) return fail(MMOT_ERR_INVALID_ARG, "NULL argument");
-    if (kernel < 0 || kernel > 6) return fail(MMOT_ERR_INVALID_ARG, "kernel must be in 0..6");
+    if (kernel < 0 || kernel > 7) return fail(MMOT_ERR_INVALID_ARG, "kernel must be in 0..7");
     CUDA_TRY(cudaStreamSynchronize(p->st));
     for (auto &r : p->recs) {
         float ms = 0.f;

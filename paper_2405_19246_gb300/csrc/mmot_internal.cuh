@@ -108,6 +108,9 @@ struct SweepArgs {
     // d grid steps from the tile's first point; epos and emid are not read
     // (null: the general stream)
     const void *ugrid;
+    // warp tiles (l >= 6): backward states at the target points of the
+    // current target marginal, [target point][2^(l-1)] scaled floats
+    void *gtarg;
     // carry scan over chunks of tiles: flags [2][G][NB+1], contributions [2][G][NS]
     int *cflags;
     void *cagg;
@@ -143,6 +146,9 @@ template <int NB, typename V>
 cudaError_t launch_lagg(const SweepArgs &a, cudaStream_t s, int level, int fwd);
 template <int NB, typename V>
 cudaError_t launch_lscan(const SweepArgs &a, cudaStream_t s, int level, int fwd);
+// Backward walk of the warp-tile products (l >= 6): states at the targets.
+template <int NB, typename V>
+cudaError_t launch_wbwd(const SweepArgs &a, cudaStream_t s);
 // Transfer operator of a whole shard from the tile operators (shard.cuh):
 // lnop[2][NB + 1][2^NB] natural logarithms, device memory.
 template <int NB, typename V>

@@ -49,4 +49,9 @@
     {                                                                                  \
         return launch_wprod_impl<NB_, V_>(a, s);                                       \
     }                                                                                  \
+    template <>                                                                        \
+    cudaError_t launch_wbwd<NB_, V_>(const SweepArgs &a, cudaStream_t s)               \
+    {                                                                                  \
+        return launch_wbwd_impl<NB_, V_>(a, s);                                        \
+    }                                                                                  \
     }

@@ -454,13 +454,43 @@ __global__ void __launch_bounds__(128) k_wpass(SweepArgs a, int SL, int fwd_i)
     }
 }
 
-// One tile of a marginal product (both carries known): backward pass with the
-// states at the target points in shared memory, forward pass with the
-// combine, FP64 epilogue.  One warp per block (shared memory holds the
-// backward states of up to JCAP targets).  The combine keeps each target's
-// sum as an FP32 mantissa and a binary exponent; the FP64 work (ln M, the
-// potential update, residual and objective terms) runs afterwards with one
-// target per lane.
+// Backward walk of a marginal product (backward carries known): the states at
+// every target point of the tile go to a.gtarg, [target][2^NB] scaled floats
+// (the target's local index), read by k_wprod.  4 warps per block, one tile
+// per warp.
+template <int NB, typename V>
+__global__ void __launch_bounds__(128) k_wbwd(SweepArgs a)
+{
+    using R = WarpRun<NB, V>;
+    constexpr int NS = 1 << NB;
+    constexpr int NQ = R::NQ;
+    const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (b >= a.nt) return;
+    if (a.frozen && (a.mode == MODE_UPDATE || a.mode == MODE_RESIDUAL) && a.frozen[a.seg[b]]) return;
+    __shared__ V fbuf[4][32][16];
+    __shared__ long long fxt[4][2 * NB + 1];
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const uint32_t t0 = a.tstart[b];
+    const int n = (int)(a.tstart[b + 1] - t0);
+    const int nt = warp_count_targets(a, t0, n, a.j);
+    double beta[NB];
+    warp_betas<NB>(a, b, a.j, beta);
+    SfT<V> *G = sfp<V>(a.gtarg) + (size_t)a.cnt[(size_t)b * a.l + a.j] * NS;
+    R rb;
+    rb.init(a, b);
+    rb.setup_fx(beta, fxt[wv]);
+    rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
+    rb.run(a, t0, n, a.j, false, nt, fbuf[wv], [&](int slot, V) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) G[(size_t)slot * NS + lane + 32 * q] = sf_store(rb.f[q]);
+    });
+}
+
+// One tile of a marginal product (both carries known; the backward states at
+// the targets from k_wbwd): forward pass with the combine, FP64 epilogue.
+// One warp per block.  The combine keeps each target's sum as an FP32
+// mantissa and a binary exponent; the FP64 work (ln M, the potential update,
+// residual and objective terms) runs afterwards with one target per lane.
 template <int NB, typename V>
 __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
 {
@@ -469,7 +499,6 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     constexpr int NQ = R::NQ;
     constexpr int JCAP = WShape<NB, V>::JCAP;
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ SfT<V> Gt[JCAP * NS];
     __shared__ V tsw[JCAP];      // per target: sum mantissa (0: M = 0)
     __shared__ int tew[JCAP];    // per target: binary exponent of the sum
     __shared__ double gq[JCAP];  // per target: new g/eps (update)
@@ -496,16 +525,11 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
     const double eps_b = tile_eps(a, b);
     const double inv_eps_b = a.teps ? 1.0 / eps_b : a.inv_eps;
 
-    // backward states at the target points
+    // the backward states at the target points (k_wbwd)
+    const SfT<V> *Gt = sfp<V>(a.gtarg) + (size_t)a.cnt[(size_t)b * a.l + a.j] * NS;
     R rb;
     rb.init(a, b);
     rb.setup_fx(beta, fxt);
-    rb.load_carries(sfp<V>(a.bcarry), b, beta, NB + 1);
-    rb.run(a, t0, n, a.j, false, nt, fbuf, [&](int slot, V) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) Gt[slot * NS + lane + 32 * q] = sf_store(rb.f[q]);
-    });
-    __syncwarp();
 
     // Per-level factor of the combine, exp(gamma_s + gamma_{NB-s} - w_s pF -
     // w_{NB-s} pG) with pG = span - pF:  exp(K_s - a_s pF), K_s = gamma_s +
@@ -571,7 +595,7 @@ __global__ void __launch_bounds__(32) k_wprod(SweepArgs a)
             const V ems = __shfl_sync(FULL, em, s);
             const Sf<V> fS = (S == 0) ? Sf<V>{V(0.5), 1} : rf.f[q];
             const int U = (NS - 1) ^ S;
-            const Sf<V> gU = (U == 0) ? Sf<V>{V(0.5), 1} : sf_load<V>(Gt[slot * NS + U]);
+            const Sf<V> gU = (U == 0) ? Sf<V>{V(0.5), 1} : sf_load<V>(__ldcg(Gt + (size_t)slot * NS + U));
             if (fS.m != V(0) && gU.m != V(0)) {
                 const Sf<V> z = sf_make<V>(fS.m * gU.m * ems);
                 const int E = z.k + fS.k + gU.k + ens;
@@ -857,6 +881,13 @@ template <int NB, typename V>
 cudaError_t launch_wprod_impl(const SweepArgs &a, cudaStream_t st)
 {
     k_wprod<NB, V><<<a.nt, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NB, typename V>
+cudaError_t launch_wbwd_impl(const SweepArgs &a, cudaStream_t st)
+{
+    k_wbwd<NB, V><<<(a.nt + 3) / 4, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
