@@ -207,7 +207,8 @@ struct mmot_plan_s {
     int ops_target = -1;       // target whose tile operators are current
     double *partial = nullptr;
     double *part4 = nullptr;   // [nt*4] per-tile objective sums
-    double *d_obj = nullptr;   // [nseg*5] per instance: mass, residual, primal, g mu, W
+    double *d_obj = nullptr;   // [nseg*6] per instance: mass, residual (all l), primal, g mu, W,
+                               // residual of the stopping test (marginals 1..l-1)
     int *flags = nullptr;   // flags followed by the tile counter
     size_t flags_bytes = 0;
     int *err = nullptr;
@@ -692,7 +693,7 @@ __global__ void k_reset_seg(double *g, const int64_t *off, const double *g0, int
 // transport cost W = Z * sum of the per-tile W_b / Z_b (partial) into
 // acc[q*5 + 4], Z from ln Z of the instance's first tile.
 __global__ void k_seg_obj(const double *part4, const double *partial, const double *w_lnz, const int32_t *t0,
-                          double *acc, int set_mass)
+                          double *acc, int set_mass, int stop)
 {
     const int q = blockIdx.x;
     const int b0 = t0[q], b1 = t0[q + 1];
@@ -721,11 +722,12 @@ __global__ void k_seg_obj(const double *part4, const double *partial, const doub
             }
             if (w_lnz) {
                 const double lz = w_lnz[b0];
-                acc[(size_t)q * 5 + 4] = (lz == -INFINITY) ? 0.0 : S * exp(lz);
+                acc[(size_t)q * 6 + 4] = (lz == -INFINITY) ? 0.0 : S * exp(lz);
             } else if (m == 0) {
-                if (set_mass) acc[(size_t)q * 5 + 0] = S;
+                if (set_mass) acc[(size_t)q * 6 + 0] = S;
             } else {
-                acc[(size_t)q * 5 + m] += S;
+                acc[(size_t)q * 6 + m] += S;
+                if (m == 1 && stop) acc[(size_t)q * 6 + 5] += S;
             }
         }
     }
@@ -1181,7 +1183,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     }
     PA(p->partial, nt);
     PA(p->part4, (size_t)nt * 4);
-    PA(p->d_obj, (size_t)nin * 5);
+    PA(p->d_obj, (size_t)nin * 6);
     if (!batch) PA(p->d_segt0, 2);
     p->flags_bytes = sizeof(int) * ((size_t)nt * (p->NB + 1) + 1);
     PA(p->flags, (size_t)nt * (p->NB + 1) + 1);
@@ -1352,15 +1354,17 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
 // (FP64), a compensated per-instance reduction follows, and the transport cost
 // comes from the objective sweeps; only five FP64 values per instance reach
 // the host.
-mmot_status plan_objective(mmot_plan p, std::vector<mmot_result> &R)
+// stop_res (optional): per instance the residual of the stopping test
+// (marginals 1..l-1) from the same products
+mmot_status plan_objective(mmot_plan p, std::vector<mmot_result> &R, std::vector<double> *stop_res = nullptr)
 {
     const int l = p->l, ns = p->nseg;
     R.assign(ns, mmot_result{});
-    CUDA_TRY(cudaMemsetAsync(p->d_obj, 0, sizeof(double) * 5 * ns, p->st));
+    CUDA_TRY(cudaMemsetAsync(p->d_obj, 0, sizeof(double) * 6 * ns, p->st));
     for (int k = 0; k < l; ++k) {
         mmot_status s = enqueue_product(p, k, MODE_OBJ, nullptr);
         if (s != MMOT_OK) return s;
-        k_seg_obj<<<ns, 256, 0, p->st>>>(p->part4, nullptr, nullptr, p->d_segt0, p->d_obj, k == l - 1);
+        k_seg_obj<<<ns, 256, 0, p->st>>>(p->part4, nullptr, nullptr, p->d_segt0, p->d_obj, k == l - 1, k < l - 1);
         CUDA_TRY(cudaGetLastError());
         p->launches += 1;
     }
@@ -1369,16 +1373,18 @@ mmot_status plan_objective(mmot_plan p, std::vector<mmot_result> &R)
         // transport cost: per instance, Z times the sum over its tiles of eps W_b / Z_b
         mmot_status sc = enqueue_cost(p);
         if (sc != MMOT_OK) return sc;
-        k_seg_obj<<<ns, 256, 0, p->st>>>(nullptr, p->partial, p->o_lnz, p->d_segt0, p->d_obj, 0);
+        k_seg_obj<<<ns, 256, 0, p->st>>>(nullptr, p->partial, p->o_lnz, p->d_segt0, p->d_obj, 0, 0);
         CUDA_TRY(cudaGetLastError());
         p->launches += 1;
     }
-    std::vector<double> h((size_t)ns * 5);
+    std::vector<double> h((size_t)ns * 6);
     CUDA_TRY(cudaMemcpyAsync(h.data(), p->d_obj, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, p->st));
     CUDA_TRY(cudaStreamSynchronize(p->st));
+    if (stop_res) stop_res->assign(ns, 0.0);
     for (int q = 0; q < ns; ++q) {
         const double e = p->seg_eps[q];
-        const double *o = &h[(size_t)q * 5];
+        const double *o = &h[(size_t)q * 6];
+        if (stop_res) (*stop_res)[q] = o[5];
         R[q].mass = o[0];
         R[q].residual = o[1];
         R[q].primal = o[2];
@@ -1509,16 +1515,15 @@ mmot_status mmot_solve(mmot_plan p, double tol, int itr_max, mmot_result *out)
         t += n;
         if (tol > 0.0 && res <= tol) break;
     }
-    mmot_status s = mmot_objective(p, out);
+    // the objective's products give the stopping residual of the final
+    // potentials as well (no separate residual products)
+    memset(out, 0, sizeof(*out));
+    std::vector<mmot_result> R;
+    std::vector<double> stop;
+    mmot_status s = plan_objective(p, R, &stop);
     if (s != MMOT_OK) return s;
-    if (tol <= 0.0 || t == 0) {
-        double r = 0.0;
-        s = enqueue_residual(p, 0, p->l - 1);
-        if (s != MMOT_OK) return s;
-        s = read_scalar(p, p->dsum, &r);
-        if (s != MMOT_OK) return s;
-        res = r;
-    }
+    *out = R[0];
+    if (tol <= 0.0 || t == 0) res = stop[0];
     out->iters = t;
     out->residual = res;
     s = check_device_error(p);
