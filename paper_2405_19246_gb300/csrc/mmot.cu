@@ -221,6 +221,7 @@ struct mmot_plan_s {
     std::vector<unsigned char> h_odecF, h_odecB;
     unsigned char *o_opF = nullptr, *o_opB = nullptr, *o_fc = nullptr, *o_bc = nullptr;
     unsigned char *o_decF = nullptr, *o_decB = nullptr, *o_cagg = nullptr, *o_agg = nullptr, *o_inc = nullptr;
+    unsigned char *o_coef = nullptr;   // l = 8: per tile and marginal, the pair coefficient of a two-level pass
     int *o_cflags = nullptr, *o_flags = nullptr;
     size_t o_flags_bytes = 0;
     double *o_lnz = nullptr;   // [nt] ln Z seen by each tile
@@ -587,6 +588,7 @@ mmot_status ensure_objective_scratch(mmot_plan p)
         CUDA_TRY(p->alloc(&p->o_decB, p->h_odecB.size()));
         CUDA_TRY(p->alloc(&p->o_cflags, (size_t)2 * ns * 32));
         CUDA_TRY(p->alloc(&p->o_cagg, (size_t)2 * ns * 32 * sf));
+        CUDA_TRY(p->alloc(&p->o_coef, nt * (size_t)l * sf));
         CUDA_TRY(cudaMemcpyAsync(p->o_decF, p->h_odecF.data(), p->h_odecF.size(), cudaMemcpyHostToDevice, p->st));
         CUDA_TRY(cudaMemcpyAsync(p->o_decB, p->h_odecB.data(), p->h_odecB.size(), cudaMemcpyHostToDevice, p->st));
         CUDA_TRY(cudaMemsetAsync(p->o_fc, 0, nt * ns * sf, p->st));
@@ -633,16 +635,31 @@ mmot_status enqueue_cost(mmot_plan p)
     a.cflags = p->o_cflags;
     a.cagg = p->o_cagg;
     if (l == 8) {
+        // two levels per walk, as in the products: the pass of level lv also
+        // gives level lv+1 its own share and the coefficients of the share
+        // that goes through a level-lv carry
         CUDA_TRY(cudaMemsetAsync(p->o_cflags, 0, sizeof(int) * 2 * 256 * 32, p->st));
+        a.coef = p->o_coef;
+        auto lo = [&](int kind, int lv, int fwd) {
+            return fp64 ? launch_objective_warp8<double>(a, p->st, kind, lv, fwd)
+                        : launch_objective_warp8<float>(a, p->st, kind, lv, fwd);
+        };
         for (int fwd = 0; fwd < 2; ++fwd) {
-            for (int lv = 1; lv <= l; ++lv) {
-                CUDA_TRY(fp64 ? launch_objective_warp8<double>(a, p->st, 5, lv, fwd)
-                              : launch_objective_warp8<float>(a, p->st, 5, lv, fwd));
-                CUDA_TRY(fp64 ? launch_objective_warp8<double>(a, p->st, 6, lv, fwd)
-                              : launch_objective_warp8<float>(a, p->st, 6, lv, fwd));
+            for (int lv = 1; lv <= l; lv += 2) {
+                const bool pair = (lv + 1 <= l);
+                a.pair = pair ? 1 : 0;
+                CUDA_TRY(lo(5, lv, fwd));
+                a.pair = 0;
+                CUDA_TRY(lo(6, lv, fwd));
                 p->launches += 2;
+                if (pair) {
+                    a.pair = 1;
+                    CUDA_TRY(lo(6, lv + 1, fwd));
+                    p->launches += 1;
+                }
             }
         }
+        a.pair = 0;
         CUDA_TRY(fp64 ? launch_objective_warp8<double>(a, p->st, 7, 0, 0)
                       : launch_objective_warp8<float>(a, p->st, 7, 0, 0));
     } else if (l <= kMaxOpBits) {

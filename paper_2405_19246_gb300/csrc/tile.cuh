@@ -101,7 +101,12 @@ __device__ __forceinline__ float f2_exp(F2 x)
 template <typename V>
 __device__ __forceinline__ V vrcp(V x);
 template <>
-__device__ __forceinline__ float vrcp<float>(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float vrcp<float>(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <>
 __device__ __forceinline__ double vrcp<double>(double x) { return __drcp_rn(x); }
 
@@ -633,7 +638,7 @@ struct TileRun {
     __device__ __forceinline__ static void inject(V (&f)[NS], const V (&fe)[NB + 1][NB], const V (&rr)[NS][NB])
     {
         static_for<1, NS>([&](auto tc) {
-            constexpr int T = decltype(tc)::value;
+            constexpr int T = NS - decltype(tc)::value;
             V acc = f[T];
             static_for<0, NB>([&](auto kc) {
                 constexpr int kb = decltype(kc)::value;
