@@ -250,6 +250,28 @@ __device__ __forceinline__ Sf<V> sf_warp_sum(Sf<V> a)
     return r;
 }
 
+// sf_warp_sum with rolled shuffle rounds: for code that runs once per warp,
+// where fetching the instructions costs more than the loop overhead
+template <typename V>
+__device__ __forceinline__ Sf<V> sf_warp_sum_rolled(Sf<V> a)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    int kmax = (a.m == V(0)) ? INT_MIN : a.k;
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+    if (kmax == INT_MIN) return sf_zero<V>();
+    V m = (a.m == V(0)) ? V(0) : a.m * pow2neg<V>(a.k - kmax);
+#pragma unroll 1
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = __shfl_down_sync(FULL, m, o);
+        if ((threadIdx.x & 31) + o < 32) m += y;
+    }
+    m = __shfl_sync(FULL, m, 0);
+    Sf<V> r = sf_make<V>(m);
+    r.k += kmax;
+    return r;
+}
+
 // storage form of a scaled float
 template <typename V>
 struct SfSt;
@@ -1359,7 +1381,7 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
             }
         }
         // block scan of the maps (inclusive in the warp, then across warps)
-#pragma unroll
+#pragma unroll 1
         for (int o = 1; o < 32; o <<= 1) {
             Sf<V> oa;
             oa.m = __shfl_up_sync(FULL, am.m, o);
@@ -1406,7 +1428,7 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
 #pragma unroll
             for (int T = 1; T < NS; ++T)
                 if (popc_c(T) == s) wb[T] = (lane < NWB) ? Sf<V>{s_m[lane][T], s_k[lane][T]} : sf_zero<V>();
-#pragma unroll
+#pragma unroll 1
             for (int o = 1; o < 32; o <<= 1) {
                 Sf<V> oa;
                 oa.m = __shfl_up_sync(FULL, wa.m, o);
@@ -1481,7 +1503,7 @@ __global__ void __launch_bounds__(256) k_carry(SweepArgs a)
 #pragma unroll
             for (int T = 1; T < NS; ++T) {
                 if (popc_c(T) == s) {
-                    const Sf<V> t = sf_warp_sum(part[T]);
+                    const Sf<V> t = sf_warp_sum_rolled(part[T]);
                     if (lane == 0) {
                         s_em[T] = t.m;
                         s_ek[T] = t.k;
