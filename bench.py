@@ -50,11 +50,13 @@ WORKLOADS = {
                  desc="l=3, N=1000 uniform grid, Gaussian-mixture weights, eps=1e-2, 200 iterations"),
 }
 
-# DRAM traffic per k_fwd launch from one ncu capture, tied to the kernel source
-# it was measured on (null when the source has changed since).
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes.sum.per_second x gpu__time_duration.sum, sections SpeedOfLight
+# and MemoryWorkloadAnalysis, cold cache), keyed by (workload, precision,
+# kernel, hash of the kernel sources it was measured on): a source change
+# since the capture gives null.
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum, one k_prod launch (cold cache)
-
+    ("large", "fp32", "k_tile", "3aeb52f3f24cb9cb"): 100.4e6,   # 665.8 GB/s x 150.8 us
 }
 
 
