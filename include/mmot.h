@@ -356,6 +356,17 @@ mmot_status mmot_batch_status(mmot_batch b, int i, int *iters, double *residual,
 /* Potentials g_k of instance i (N_k FP64, host or device). */
 mmot_status mmot_batch_get_potentials(mmot_batch b, int i, int k, double *g_out);
 
+/* Replace the potentials g_k of instance i (N_k FP64, host or device; the
+ * call is synchronous and orders a device input after all work queued on
+ * the device).  A warm start: the Sinkhorn state of an instance is its l
+ * potentials (Algorithm 1 updates one g_k at a time from the others), so
+ * setting all l of them from another run continues that run at an iteration
+ * boundary.  A frozen or converged instance becomes active again (status:
+ * converged = 0, residual NaN until the next check).  Errors:
+ * MMOT_ERR_INVALID_ARG for a NULL pointer, an index out of range or a NaN /
+ * +inf value (the batch is unchanged); MMOT_ERR_CUDA for a failed copy. */
+mmot_status mmot_batch_set_potentials(mmot_batch b, int i, int k, const double *g_in);
+
 typedef struct {
     int instances;
     int groups;                /* launch groups: one per l, split into parts when

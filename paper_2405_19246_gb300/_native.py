@@ -34,7 +34,7 @@ EXPORTED = [
     "mmot_shard_create", "mmot_shard_operator", "mmot_shard_set_inflow", "mmot_shard_update", "mmot_shard_residual",
     "mmot_ftvp2d",
     "mmot_batch_create", "mmot_batch_step", "mmot_batch_reset", "mmot_batch_solve", "mmot_batch_freeze", "mmot_batch_status",
-    "mmot_batch_get_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
+    "mmot_batch_get_potentials", "mmot_batch_set_potentials", "mmot_batch_get_info", "mmot_batch_destroy",
     "mmot_destroy", "mmot_last_error",
 ]
 
@@ -104,6 +104,7 @@ def lib():
         L.mmot_batch_freeze.argtypes = [vp, i]
         L.mmot_batch_status.argtypes = [vp, i, P(i), P(d), P(i)]
         L.mmot_batch_get_potentials.argtypes = [vp, i, i, vp]
+        L.mmot_batch_set_potentials.argtypes = [vp, i, i, vp]
         L.mmot_batch_get_info.argtypes = [vp, P(MmotBatchInfo)]
         L.mmot_batch_destroy.argtypes = [vp]
         L.mmot_destroy.argtypes = [vp]

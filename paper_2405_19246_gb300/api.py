@@ -252,6 +252,13 @@ class Batch:
         nat.check(nat.lib().mmot_batch_get_potentials(self._h, int(i), int(k), g.ctypes.data))
         return g
 
+    def set_potentials(self, i, k, g):
+        """Replace g_k of instance i (a warm start; see mmot_batch_set_potentials)."""
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        if g.shape != (self.N[i][k],):
+            raise ValueError("instance %d, marginal %d takes %d potentials" % (i, k, self.N[i][k]))
+        nat.check(nat.lib().mmot_batch_set_potentials(self._h, int(i), int(k), g.ctypes.data))
+
     def info(self):
         inf = nat.MmotBatchInfo()
         nat.check(nat.lib().mmot_batch_get_info(self._h, ctypes.byref(inf)))

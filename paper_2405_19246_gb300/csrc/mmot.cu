@@ -896,11 +896,17 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
 {
     const int l = p->l;
     const int nt = p->nt;
+    // 1/eps of every point of marginal k: each instance of a batch has its own eps
+    std::vector<double> ie((size_t)p->N[k], 1.0 / p->eps);
+    if (p->nseg > 1 && p->seg_off.size() == (size_t)(p->nseg + 1) * l)
+        for (int q = 0; q < p->nseg; ++q)
+            for (int64_t i = p->seg_off[(size_t)q * l + k]; i < p->seg_off[(size_t)(q + 1) * l + k]; ++i)
+                ie[(size_t)i] = 1.0 / p->seg_eps[q];
     std::vector<double> bmax(nt, -INFINITY);
     for (int64_t i = 0; i < p->N[k]; ++i) {
         const uint32_t t = p->h_mpos[k][i];
         const uint32_t b = p->h_tile_of[t];
-        bmax[b] = std::max(bmax[b], g[i] / p->eps);
+        bmax[b] = std::max(bmax[b], g[i] * ie[i]);
     }
     for (int b = 0; b < nt; ++b) {
         double v = bmax[b];
@@ -914,7 +920,7 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
     for (int64_t i = 0; i < p->N[k]; ++i) {
         const uint32_t t = p->h_mpos[k][i];
         const uint32_t b = p->h_tile_of[t];
-        const double v = g[i] / p->eps - p->h_beta[(size_t)b * l + k];
+        const double v = g[i] * ie[i] - p->h_beta[(size_t)b * l + k];
         if (p->esz == 8)
             reinterpret_cast<double *>(lp.data())[t] = v;
         else
@@ -930,7 +936,7 @@ mmot_status upload_potential(mmot_plan p, int k, const std::vector<double> &g)
             const uint32_t t = p->h_mpos[k][i];
             const uint32_t b = p->h_tile_of[t];
             const size_t u = (size_t)p->h_toff[b] + (t - p->h_tstart[b]);
-            const double v = std::exp(g[i] / p->eps - p->h_beta[(size_t)b * l + k]);
+            const double v = std::exp(g[i] * ie[i] - p->h_beta[(size_t)b * l + k]);
             if (p->esz == 8)
                 reinterpret_cast<double *>(ep.data())[u] = v;
             else
@@ -2091,6 +2097,43 @@ mmot_status mmot_batch_get_potentials(mmot_batch b, int i, int k, double *g_out)
     const int64_t n = p->seg_off[(size_t)(q + 1) * p->l + k] - o;
     CUDA_TRY(cudaMemcpyAsync(g_out, p->g[k] + o, sizeof(double) * n, cudaMemcpyDefault, p->st));
     CUDA_TRY(cudaStreamSynchronize(p->st));
+    return MMOT_OK;
+}
+
+mmot_status mmot_batch_set_potentials(mmot_batch b, int i, int k, const double *g_in)
+{
+    if (!b || !g_in) return fail(MMOT_ERR_INVALID_ARG, "NULL batch or input");
+    if (i < 0 || i >= b->n) return fail(MMOT_ERR_INVALID_ARG, "instance %d out of range", i);
+    auto &G = b->groups[b->where[i].first];
+    const int q = b->where[i].second;
+    mmot_plan p = G.p;
+    if (k < 0 || k >= p->l) return fail(MMOT_ERR_INVALID_ARG, "marginal %d out of range", k);
+    const int64_t o = p->seg_off[(size_t)q * p->l + k];
+    const int64_t n = p->seg_off[(size_t)(q + 1) * p->l + k] - o;
+    std::vector<double> gi((size_t)n);
+    if (is_device_ptr(g_in)) CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpyAsync(gi.data(), g_in, sizeof(double) * n, cudaMemcpyDefault, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    for (int64_t t = 0; t < n; ++t)
+        if (std::isnan(gi[t]) || gi[t] == INFINITY)
+            return fail(MMOT_ERR_INVALID_ARG, "g[%lld] is NaN or +inf", (long long)t);
+    // the group's marginal k with this instance's slice replaced, then the
+    // host re-centring of the whole marginal (ln phi and e^{ln phi} streams)
+    std::vector<double> g((size_t)p->N[k]);
+    CUDA_TRY(cudaMemcpyAsync(g.data(), p->g[k], sizeof(double) * p->N[k], cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(cudaStreamSynchronize(p->st));
+    std::copy(gi.begin(), gi.end(), g.begin() + o);
+    mmot_status s = upload_potential(p, k, g);
+    if (s != MMOT_OK) return s;
+    if (G.conv[q] || G.frozen_only[q]) {
+        G.conv[q] = 0;
+        G.frozen_only[q] = 0;
+        G.active += 1;
+        const int32_t zero = 0;
+        CUDA_TRY(cudaMemcpyAsync(p->d_frozen + q, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, p->st));
+        CUDA_TRY(cudaStreamSynchronize(p->st));
+    }
+    G.res[q] = NAN;
     return MMOT_OK;
 }
 

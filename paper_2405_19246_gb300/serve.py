@@ -9,12 +9,18 @@ at different times overlap on the device.  Potentials stay resident in the
 cohort's device memory between iterations; after every ``check_every``
 iterations the per-instance residuals come back and an instance whose
 residual is at most ``tol`` (or whose iteration budget is spent) finishes:
-its result is recorded and it stops receiving updates.  A cohort whose
-instances have all finished releases its memory.
+its result is recorded and it stops receiving updates.
+
+Finished instances give their memory back at the next check: when requests
+are waiting, the cohort takes the oldest of them that fit into the memory of
+its finished instances (plus any unused budget) and re-forms its batch from
+its unfinished instances, warm-started from their current potentials
+(``Batch.set_potentials``: an instance's Sinkhorn state is its l potentials,
+so it continues at an iteration boundary with its iteration count carried
+over), and the newly joined requests.  A cohort whose instances have all
+finished with no request waiting releases its memory.
 
 The scheduling is host logic; every computation runs in the CUDA library.
-Requests are not merged into a running cohort (a cohort's merged layout is
-fixed when it is created).
 """
 from __future__ import annotations
 
@@ -66,19 +72,29 @@ def estimate_bytes(req: Request, precision: str = "fp32") -> int:
 
 
 class Cohort:
-    """Requests admitted together: one batch, one stream, one stepping thread."""
+    """Requests admitted together: one batch, one stream, one stepping thread.
+
+    refill(cohort, freed_bytes) (optional) returns waiting requests that
+    join the cohort at a check where some of its instances have finished."""
 
     def __init__(self, reqs: List[Request], make_batch: Callable, tol: float, itr_max: int,
-                 check_every: int, keep_potentials: bool, on_done: Callable):
+                 check_every: int, keep_potentials: bool, on_done: Callable,
+                 refill: Optional[Callable] = None, precision: str = "fp32"):
         self.reqs = reqs
+        self.make_batch = make_batch
         self.tol = tol
         self.itr_max = itr_max
         self.check_every = check_every
         self.keep_potentials = keep_potentials
         self.on_done = on_done
+        self.refill = refill
+        self.precision = precision
         self.batch = make_batch(reqs)
         self.done = [False] * len(reqs)
-        self.iters = 0
+        self.base = [0] * len(reqs)   # iterations each request ran before this batch
+        self.iters = 0                # iterations of the current batch
+        self.released = 0             # finished requests whose memory is not yet reused
+        self.regroups = 0
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.error: Optional[BaseException] = None
 
@@ -88,14 +104,34 @@ class Cohort:
     def _finish(self, i, now):
         r = self.reqs[i]
         st = self.batch.status(i)
-        r.iters = st["iters"] if st["converged"] else self.iters
+        r.iters = self.base[i] + (st["iters"] if st["converged"] else self.iters)
         r.residual = st["residual"]
         r.converged = st["converged"]
         if self.keep_potentials:
             r.potentials = [self.batch.get_potentials(i, k) for k in range(r.l)]
         r.finished = now
         self.done[i] = True
+        self.released += estimate_bytes(r, self.precision)
         self.on_done(r)
+
+    def _regroup(self, joining: List[Request]):
+        """New batch: the unfinished instances, warm-started, then the joining requests."""
+        keep = [i for i in range(len(self.reqs)) if not self.done[i]]
+        carried = [(self.reqs[i], self.base[i] + self.iters,
+                    [self.batch.get_potentials(i, k) for k in range(self.reqs[i].l)]) for i in keep]
+        self.batch.close()
+        self.batch = None
+        reqs = [c[0] for c in carried] + list(joining)
+        self.batch = self.make_batch(reqs)
+        for i, (_, _, gs) in enumerate(carried):
+            for k, g in enumerate(gs):
+                self.batch.set_potentials(i, k, g)
+        self.reqs = reqs
+        self.done = [False] * len(reqs)
+        self.base = [c[1] for c in carried] + [0] * len(joining)
+        self.iters = 0
+        self.released = 0
+        self.regroups += 1
 
     def _loop(self):
         try:
@@ -108,13 +144,18 @@ class Cohort:
                         continue
                     if self.batch.status(i)["converged"]:
                         self._finish(i, now)
-                    elif self.iters >= self.itr_max:
+                    elif self.base[i] + self.iters >= self.itr_max:
                         self.batch.freeze(i)
                         self._finish(i, now)
+                if self.refill is not None and self.released > 0:
+                    joining = self.refill(self, self.released, sum(not d for d in self.done))
+                    if joining:
+                        self._regroup(joining)
         except BaseException as e:   # surfaced by Server.run
             self.error = e
         finally:
-            self.batch.close()
+            if self.batch is not None:
+                self.batch.close()
 
 
 class Server:
@@ -127,7 +168,7 @@ class Server:
 
     def __init__(self, precision="fp32", tol=1e-6, itr_max=10000, check_every=20,
                  mem_budget=64 << 30, max_cohort=4096, keep_potentials=False, make_batch=None,
-                 tick=0.002, tile_caps=None):
+                 tick=0.002, tile_caps=None, regroup=True):
         self.precision = precision
         self.tol = tol
         self.itr_max = itr_max
@@ -146,6 +187,9 @@ class Server:
         self.used = 0
         self.lock = threading.Lock()
         self.admissions = 0
+        # requests that joined a running cohort (its finished instances' memory)
+        self.regroup = regroup
+        self.joined = 0
 
     def _default_batch(self, reqs):
         import torch
@@ -182,12 +226,35 @@ class Server:
         for r in take:
             r.admitted = now
         c = Cohort(take, self.make_batch, self.tol, self.itr_max, self.check_every,
-                   self.keep_potentials, self._on_done)
+                   self.keep_potentials, self._on_done,
+                   refill=self._refill if self.regroup else None, precision=self.precision)
         c.mem = mem
         self.used += mem
         self.cohorts.append(c)
         self.admissions += 1
         c.start()
+
+    def _refill(self, cohort, freed, active):
+        """Waiting requests, oldest first, that fit into the memory of the
+        cohort's finished instances plus the unused budget (called from the
+        cohort's thread at a check)."""
+        take, mem = [], 0
+        with self.lock:
+            room = self.mem_budget - self.used + freed
+            while self.waiting and active + len(take) < self.max_cohort:
+                b = estimate_bytes(self.waiting[0], self.precision)
+                if mem + b > room:
+                    break
+                take.append(self.waiting.popleft())
+                mem += b
+            if take:
+                self.used += mem - freed
+                cohort.mem += mem - freed
+                self.joined += len(take)
+        now = time.perf_counter()
+        for r in take:
+            r.admitted = now
+        return take
 
     def _reap(self):
         for c in list(self.cohorts):

@@ -138,7 +138,7 @@ def test_served_result_same_alone_and_in_mix(api):
         return Request(rid=i, xs=xs, mus=mus, eps=eps)
 
     alone = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True).run([(0.0, req(4))])
-    mix = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True, max_cohort=3)
+    mix = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True, max_cohort=3, regroup=False)
     res = {r.rid: r for r in mix.run([(0.005 * i, req(i)) for i in range(10)])}
     a, m = alone[0], res[4]
     assert len(res) == 10 and mix.admissions >= 2
@@ -147,3 +147,73 @@ def test_served_result_same_alone_and_in_mix(api):
     for k in range(len(inst[4][0])):
         d = np.max(np.abs(a.potentials[k] - m.potentials[k])) / eps
         assert d <= 2e-4, (k, d)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_warm_start_continues_the_run(api, prec):
+    """Potentials of an instance moved into another batch (set_potentials on
+    all l marginals) continue its run: a few more iterations there give what
+    the original batch gives."""
+    # one l, so the moved instance shares its launch group with instances of
+    # other eps and is not the group's first
+    inst = _mixed_instances(4, seed=908, N_range=(40, 500), eps_range=(2e-2, 1e-1), l_range=(4, 4))
+    other = _mixed_instances(5, seed=909, N_range=(40, 500), eps_range=(2e-2, 1e-1), l_range=(4, 4))
+    q, j = 2, 3
+    with api.Batch(inst, precision=prec) as A:
+        A.step(5, 0.0)
+        gs = [A.get_potentials(q, k) for k in range(len(inst[q][0]))]
+        with api.Batch(other[:j] + [inst[q]] + other[j:], precision=prec) as B:
+            assert B.info()["groups"] == 1
+            for k, g in enumerate(gs):
+                B.set_potentials(j, k, g)
+            for k, g in enumerate(gs):
+                np.testing.assert_array_equal(B.get_potentials(j, k), g)
+            A.step(4, 0.0)
+            B.step(4, 0.0)
+            eps = inst[q][2]
+            for k in range(len(gs)):
+                d = np.max(np.abs(A.get_potentials(q, k) - B.get_potentials(j, k))) / eps
+                assert d <= TOL_G[prec], (k, d)
+
+
+def test_set_potentials_reactivates_and_rejects_nan(api):
+    inst = _mixed_instances(6, seed=910, N_range=(40, 300), eps_range=(2e-2, 1e-1), l_range=(3, 5))
+    with api.Batch(inst, precision="fp32") as B:
+        B.step(2, 0.0)
+        B.freeze(1)
+        g = B.get_potentials(1, 0)
+        bad = g.copy()
+        bad[len(bad) // 2] = np.nan
+        with pytest.raises(Exception):
+            B.set_potentials(1, 0, bad)
+        np.testing.assert_array_equal(B.get_potentials(1, 0), g)
+        B.set_potentials(1, 0, g)
+        before = B.get_potentials(1, 1)
+        B.step(2, 0.0)
+        assert np.max(np.abs(B.get_potentials(1, 1) - before)) > 0.0   # updated again
+
+
+def test_served_requests_join_a_running_cohort(api):
+    """A memory budget of two and a half requests of one size: two start,
+    the rest join the running cohort as its instances finish; every request
+    converges and matches the same request solved alone."""
+    from paper_2405_19246_gb300.serve import Request, Server, estimate_bytes
+    inst = _mixed_instances(6, seed=911, N_range=(200, 200), eps_range=(3e-2, 1e-1), l_range=(4, 4))
+
+    def req(i):
+        xs, mus, eps = inst[i]
+        return Request(rid=i, xs=xs, mus=mus, eps=eps)
+
+    budget = int(2.5 * max(estimate_bytes(req(i)) for i in range(6)))
+    srv = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True, mem_budget=budget)
+    res = {r.rid: r for r in srv.run([(0.0, req(i)) for i in range(6)])}
+    assert len(res) == 6 and all(r.converged for r in res.values())
+    assert srv.joined >= 1
+    for i in (0, 5):
+        a = Server(tol=1e-5, itr_max=4000, check_every=10, keep_potentials=True).run([(0.0, req(i))])[0]
+        m = res[i]
+        assert abs(a.iters - m.iters) <= 10, (i, a.iters, m.iters)
+        eps = inst[i][2]
+        for k in range(len(inst[i][0])):
+            d = np.max(np.abs(a.potentials[k] - m.potentials[k])) / eps
+            assert d <= 1e-3, (i, k, d)

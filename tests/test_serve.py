@@ -10,28 +10,33 @@ from paper_2405_19246_gb300.serve import Request, Server, estimate_bytes, latenc
 
 
 class FakeBatch:
-    """Instance i converges after need[i] iterations (residual 1/(1+iters))."""
+    """Instance i converges after need[i] iterations (residual 1/(1+iters)).
+    Its "potentials" carry (rid, iterations run so far), so a warm start
+    through set_potentials resumes its progress."""
 
     live = 0
     peak = 0
+    created = 0
     lock = threading.Lock()
 
     def __init__(self, reqs, need):
         self.reqs = reqs
         self.need = [need[r.rid] for r in reqs]
         self.it = 0
+        self.offset = [0] * len(reqs)
         self.frozen = [False] * len(reqs)
         self.conv = [False] * len(reqs)
         self.conv_it = [0] * len(reqs)
         with FakeBatch.lock:
             FakeBatch.live += 1
+            FakeBatch.created += 1
             FakeBatch.peak = max(FakeBatch.peak, FakeBatch.live)
 
     def step(self, n, tol):
         time.sleep(0.001)
         self.it += n
         for i, nd in enumerate(self.need):
-            if not self.conv[i] and not self.frozen[i] and self.it >= nd:
+            if not self.conv[i] and not self.frozen[i] and self.offset[i] + self.it >= nd:
                 self.conv[i] = True
                 self.conv_it[i] = self.it
         return sum(not (c or f) for c, f in zip(self.conv, self.frozen))
@@ -44,7 +49,11 @@ class FakeBatch:
         self.frozen[i] = True
 
     def get_potentials(self, i, k):
-        return np.full(3, float(self.reqs[i].rid))
+        return np.array([float(self.reqs[i].rid), float(self.offset[i] + self.it)])
+
+    def set_potentials(self, i, k, g):
+        assert g[0] == self.reqs[i].rid
+        self.offset[i] = int(g[1])
 
     def close(self):
         with FakeBatch.lock:
@@ -61,7 +70,7 @@ def test_all_requests_finish_in_budget_and_order():
     FakeBatch.peak = 0
     per = estimate_bytes(reqs[0])
     srv = Server(check_every=10, itr_max=1000, mem_budget=4 * per, max_cohort=3,
-                 make_batch=lambda rs: FakeBatch(rs, need), keep_potentials=True)
+                 make_batch=lambda rs: FakeBatch(rs, need), keep_potentials=True, regroup=False)
     arrivals = [(0.0005 * i, r) for i, r in enumerate(reqs)]
     done = srv.run(arrivals)
     assert len(done) == 40 and all(r.converged for r in done)
@@ -76,6 +85,43 @@ def test_all_requests_finish_in_budget_and_order():
         assert r.potentials[0][0] == r.rid
         assert r.iters == need[r.rid]
         assert r.finished >= r.admitted >= r.arrival
+
+
+def test_finished_instances_make_room_for_waiting_requests():
+    """With regrouping, waiting requests join the running cohort as its
+    instances finish; unfinished instances continue from their potentials
+    with their iteration counts carried over."""
+    reqs = _reqs(12)
+    need = {r.rid: (40 if r.rid % 3 else 130) for r in reqs}
+    FakeBatch.peak = 0
+    FakeBatch.created = 0
+    per = estimate_bytes(reqs[0])
+    srv = Server(check_every=10, itr_max=1000, mem_budget=4 * per, max_cohort=4,
+                 make_batch=lambda rs: FakeBatch(rs, need), keep_potentials=True)
+    done = srv.run([(0.0, r) for r in reqs])
+    assert len(done) == 12 and all(r.converged for r in done)
+    # one cohort: everything after the first four joined it as room appeared
+    assert srv.admissions == 1 and srv.joined == 8
+    assert FakeBatch.peak == 1 and FakeBatch.created > 1
+    assert srv.used == 0
+    for r in done:
+        assert r.iters == need[r.rid]
+        assert r.potentials[0][0] == r.rid and r.potentials[0][1] == need[r.rid]
+    adm = sorted(reqs, key=lambda r: (r.admitted, r.rid))
+    assert [r.rid for r in adm] == sorted(r.rid for r in adm)
+
+
+def test_regrouped_requests_keep_their_iteration_budget():
+    reqs = _reqs(6)
+    need = {r.rid: (20 if r.rid < 3 else 10 ** 9) for r in reqs}
+    per = estimate_bytes(reqs[0])
+    srv = Server(check_every=10, itr_max=60, mem_budget=4 * per, max_cohort=4,
+                 make_batch=lambda rs: FakeBatch(rs, need))
+    done = srv.run([(0.0, r) for r in reqs])
+    assert len(done) == 6 and srv.joined == 2
+    for r in done:
+        assert r.converged == (r.rid < 3)
+        assert r.iters == (20 if r.rid < 3 else 60)
 
 
 def test_iteration_budget_ends_unconverged_requests():
