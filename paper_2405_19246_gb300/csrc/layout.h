@@ -12,25 +12,56 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <thread>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "mmot_internal.cuh"
 
 namespace mmot {
 
+// Allocator whose resize leaves new elements of a trivial type uninitialised:
+// the per-point layout arrays are written once, in parallel, by the threads
+// that own their parts, so a value-initialising resize would only zero them
+// serially first (and take every page fault on one thread).
+template <typename T>
+struct DefaultInit : std::allocator<T> {
+    using std::allocator<T>::allocator;
+    DefaultInit() = default;
+    template <typename U>
+    DefaultInit(const DefaultInit<U> &) noexcept {}
+    template <typename U>
+    struct rebind {
+        using other = DefaultInit<U>;
+    };
+    template <typename U>
+    void construct(U *p) noexcept(std::is_nothrow_default_constructible<U>::value)
+    {
+        ::new (static_cast<void *>(p)) U;
+    }
+    template <typename U, typename... A>
+    void construct(U *p, A &&...a)
+    {
+        ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <typename T>
+using HVec = std::vector<T, DefaultInit<T>>;
+
 struct HostLayout {
     int l = 0;
     int64_t T = 0;
     int nt = 0;
-    std::vector<double> xm;                  // merged coordinates
-    std::vector<uint8_t> mid;                // marginal of each merged point
-    std::vector<uint32_t> mpos[MMOT_MAXL];   // merged index of each local point
+    HVec<double> xm;                         // merged coordinates
+    HVec<uint8_t> mid;                       // marginal of each merged point
+    HVec<uint32_t> mpos[MMOT_MAXL];          // merged index of each local point
     std::vector<uint32_t> tstart;            // [nt+1]
-    std::vector<uint32_t> tile_of;           // tile of each merged point
+    HVec<uint32_t> tile_of;                  // tile of each merged point
     std::vector<double> xlb, xrb;            // first / last x of each tile
     std::vector<double> ulb, urb, span;      // the same divided by eps; span = urb - ulb
-    std::vector<double> pos;                 // (x_t - xlb[tile])/eps
+    HVec<double> pos;                        // (x_t - xlb[tile])/eps
     std::vector<int32_t> cnt;                // [nt*l] points of marginal m before tile b
     std::vector<int32_t> reftile;            // [nt*l] nearest tile holding points of m
 };
@@ -207,6 +238,50 @@ inline void append_layout(HostLayout &D, const HostLayout &S, const int64_t *mar
         }
     D.T += S.T;
     D.nt += S.nt;
+}
+
+// The padded stream of the tile kernels (l <= 5): tile b's points at
+// toff[b] + (t - tstart[b]), each tile starting on a 16-element boundary and
+// the last one padded to Tp.  epos = e^{pos} (skipped when null: uniform
+// grids form it on the device), ephi = e^{ln phi} of ln phi = 0 (1 at a point,
+// 0 in the padding), emid = the point's marginal (0xff in the padding).  Every
+// element is written once, by the host thread that owns its tile.
+template <typename Tv>
+inline void fill_padded_stream(int nt, const uint32_t *tstart, const uint32_t *toff, size_t Tp, const double *pos,
+                               const uint8_t *mid, Tv *epos, Tv *ephi, uint8_t *emid)
+{
+    const int P = layout_threads((int64_t)Tp);
+    host_parallel(P, [&](int pp) {
+        for (int b = (int)((int64_t)nt * pp / P); b < (int)((int64_t)nt * (pp + 1) / P); ++b) {
+            const size_t u0 = toff[b], u1 = (b + 1 < nt) ? (size_t)toff[b + 1] : Tp;
+            const size_t n = tstart[b + 1] - tstart[b];
+            for (size_t i = 0; i < n; ++i) {
+                const size_t u = u0 + i, t = tstart[b] + i;
+                ephi[u] = Tv(1);
+                if (epos) {
+                    epos[u] = (Tv)std::exp(pos[t]);
+                    emid[u] = mid[t];
+                }
+            }
+            for (size_t u = u0 + n; u < u1; ++u) {
+                ephi[u] = Tv(0);
+                if (epos) {
+                    epos[u] = Tv(1);
+                    emid[u] = 0xff;
+                }
+            }
+        }
+    });
+}
+
+// values converted to the stream precision, on host threads
+template <typename Tv>
+inline void convert_parallel(int64_t n, const double *src, Tv *dst)
+{
+    const int P = layout_threads(n);
+    host_parallel(P, [&](int pp) {
+        for (int64_t i = n * pp / P; i < n * (pp + 1) / P; ++i) dst[i] = (Tv)src[i];
+    });
 }
 
 // exp(-w_s d) from each tile base to the next base in processing order

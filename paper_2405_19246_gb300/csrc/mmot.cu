@@ -150,9 +150,9 @@ struct mmot_plan_s {
     double *d_lnop = nullptr;   // [2][NB+1][NS]
     int64_t dev_bytes = 0;  // device memory held by this plan
     // host copies needed to re-centre potentials
-    std::vector<uint8_t> h_mid;
-    std::vector<uint32_t> h_tile_of;   // tile of each merged point
-    std::vector<uint32_t> h_mpos[MMOT_MAXL];  // merged index of each local point
+    HVec<uint8_t> h_mid;
+    HVec<uint32_t> h_tile_of;          // tile of each merged point
+    HVec<uint32_t> h_mpos[MMOT_MAXL];  // merged index of each local point
     std::vector<uint32_t> h_tstart;
     std::vector<uint32_t> h_toff;   // padded stream offset of each tile (l <= 5)
     std::vector<int32_t> h_reftile;
@@ -1097,13 +1097,15 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     // ---- merged order and tiles ----------------------------------------------
     const int nt = L.nt;
     p->nt = nt;
-    p->h_mid = L.mid;
-    for (int k = 0; k < l; ++k) p->h_mpos[k] = L.mpos[k];
-    p->h_tstart = L.tstart;
-    p->h_tile_of = L.tile_of;
-    p->h_reftile = L.reftile;
+    // the layout's arrays move into the plan (the layout is not read again)
+    p->h_mid = std::move(L.mid);
+    for (int k = 0; k < l; ++k) p->h_mpos[k] = std::move(L.mpos[k]);
+    p->h_tstart = std::move(L.tstart);
+    p->h_tile_of = std::move(L.tile_of);
+    p->h_reftile = std::move(L.reftile);
     std::vector<uint32_t> &ts = p->h_tstart;
-    std::vector<double> &hspan = L.span, &hpos = L.pos;
+    std::vector<double> &hspan = L.span;
+    HVec<double> &hpos = L.pos;
     std::vector<int32_t> &hcnt = L.cnt, &href = p->h_reftile;
     // initial baselines: g_k = -eps ln N_k of the tile's instance
     p->h_beta0.assign((size_t)nt * l, 0.0);
@@ -1227,17 +1229,15 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     auto up = [&](void *d, const void *h, size_t bytes) {
         return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, p->st);
     };
-    std::vector<unsigned char> hposb((size_t)T * p->esz), hl((size_t)T * p->esz, 0);
-    for (int64_t t = 0; t < T; ++t) {
-        if (fp64)
-            reinterpret_cast<double *>(hposb.data())[t] = hpos[t];
-        else
-            reinterpret_cast<float *>(hposb.data())[t] = (float)hpos[t];
-    }
+    HVec<unsigned char> hposb((size_t)T * p->esz);
+    if (fp64)
+        convert_parallel(T, hpos.data(), reinterpret_cast<double *>(hposb.data()));
+    else
+        convert_parallel(T, hpos.data(), reinterpret_cast<float *>(hposb.data()));
     cudaError_t ce = cudaSuccess;
     ce = ce ? ce : up(p->pos, hposb.data(), hposb.size());
     ce = ce ? ce : up(p->mid, p->h_mid.data(), T);
-    ce = ce ? ce : up(p->lphi, hl.data(), hl.size());
+    ce = ce ? ce : cudaMemsetAsync(p->lphi, 0, (size_t)T * p->esz, p->st);   // ln phi = 0
     ce = ce ? ce : up(p->tstart, ts.data(), sizeof(uint32_t) * (nt + 1));
     std::vector<double> &hulb = L.ulb, &hurb = L.urb;
     ce = ce ? ce : up(p->ulb, hulb.data(), sizeof(double) * nt);
@@ -1289,39 +1289,16 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         // padded stream: e^{pos}, scaled phi (1: lphi = 0), marginal (0xff: padding)
         const size_t Tp = (size_t)p->Tpad;
         const bool ug = (p->ugrid != nullptr);
-        std::vector<unsigned char> hep(ug ? 0 : Tp * p->esz), hph(Tp * p->esz);
-        std::vector<uint8_t> hem(ug ? 0 : Tp, 0xff);
-        // by tile, in parallel: the tile's padded range [toff[b], toff[b+1])
-        // (the last one to Tp) with padding values, then its points
-        const int P = layout_threads((int64_t)Tp);
-        host_parallel(P, [&](int pp) {
-            for (int b = (int)((int64_t)nt * pp / P); b < (int)((int64_t)nt * (pp + 1) / P); ++b) {
-                const size_t u0 = p->h_toff[b], u1 = (b + 1 < nt) ? p->h_toff[b + 1] : Tp;
-                for (size_t u = u0; u < u1; ++u) {
-                    if (fp64) {
-                        if (!ug) reinterpret_cast<double *>(hep.data())[u] = 1.0;
-                        reinterpret_cast<double *>(hph.data())[u] = 0.0;
-                    } else {
-                        if (!ug) reinterpret_cast<float *>(hep.data())[u] = 1.0f;
-                        reinterpret_cast<float *>(hph.data())[u] = 0.0f;
-                    }
-                }
-                for (uint32_t t = ts[b]; t < ts[b + 1]; ++t) {
-                    const size_t u = (size_t)p->h_toff[b] + (t - ts[b]);
-                    if (fp64)
-                        reinterpret_cast<double *>(hph.data())[u] = 1.0;
-                    else
-                        reinterpret_cast<float *>(hph.data())[u] = 1.0f;
-                    if (ug) continue;
-                    const double e = std::exp(hpos[t]);
-                    if (fp64)
-                        reinterpret_cast<double *>(hep.data())[u] = e;
-                    else
-                        reinterpret_cast<float *>(hep.data())[u] = (float)e;
-                    hem[u] = p->h_mid[t];
-                }
-            }
-        });
+        HVec<unsigned char> hep(ug ? 0 : Tp * p->esz), hph(Tp * p->esz);
+        HVec<uint8_t> hem(ug ? 0 : Tp);
+        if (fp64)
+            fill_padded_stream<double>(nt, ts.data(), p->h_toff.data(), Tp, hpos.data(), p->h_mid.data(),
+                                       ug ? nullptr : reinterpret_cast<double *>(hep.data()),
+                                       reinterpret_cast<double *>(hph.data()), ug ? nullptr : hem.data());
+        else
+            fill_padded_stream<float>(nt, ts.data(), p->h_toff.data(), Tp, hpos.data(), p->h_mid.data(),
+                                      ug ? nullptr : reinterpret_cast<float *>(hep.data()),
+                                      reinterpret_cast<float *>(hph.data()), ug ? nullptr : hem.data());
         ce = ce ? ce : up(p->toff, p->h_toff.data(), sizeof(uint32_t) * nt);
         std::vector<unsigned char> hug;
         if (ug) {
@@ -1343,12 +1320,17 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         ce = ce ? ce : up(p->ephi, hph.data(), hph.size());
         if (!fp64) {
             for (int k = 0; k < l && ce == cudaSuccess; ++k) {
-                std::vector<float2> ff(N[k]);
-                for (int64_t i = 0; i < N[k]; ++i) {
-                    const double v = hlm[k][i];
-                    const float h = (float)v;
-                    ff[i] = make_float2(h, std::isfinite(v) ? (float)(v - (double)h) : 0.0f);
-                }
+                HVec<float2> ff(N[k]);
+                const int64_t n = N[k];
+                const std::vector<double> &lm = hlm[k];
+                const int P = layout_threads(n);
+                host_parallel(P, [&](int pp) {
+                    for (int64_t i = n * pp / P; i < n * (pp + 1) / P; ++i) {
+                        const double v = lm[i];
+                        const float h = (float)v;
+                        ff[i] = make_float2(h, std::isfinite(v) ? (float)(v - (double)h) : 0.0f);
+                    }
+                });
                 ce = up(p->lnmu_ff[k], ff.data(), sizeof(float2) * N[k]);
                 // the staging vector must outlive the copy
                 if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->st);

@@ -1,10 +1,13 @@
 // Host checks of the merged-order tiling (layout.h): tie order, tile limits,
 // per-marginal counts, and the batch layout (instances one after another,
 // no decay across an instance boundary).  Prints "ok" or the first failure.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <random>
+#include <tuple>
 #include <vector>
 
 #include "layout.h"
@@ -108,6 +111,66 @@ int main()
                 CHECK(g == 0.0);
             }
         }
+
+    // above a million points the merge and the per-tile pass run on host
+    // threads in parts: the merged order must still be the sort by
+    // (x, marginal, index), with ties (a coarse grid of values) across parts
+    {
+        const int lb = 4;
+        std::mt19937_64 rng(5);
+        std::vector<std::vector<double>> z(lb);
+        int64_t Nz[4];
+        std::vector<std::tuple<double, int, int64_t>> ref;
+        for (int k = 0; k < lb; ++k) {
+            Nz[k] = 280000 + (int64_t)(rng() % 20000);
+            z[k].resize(Nz[k]);
+            for (auto &v : z[k]) v = (double)(rng() % 50000) / 50000.0;
+            std::sort(z[k].begin(), z[k].end());
+            for (int64_t i = 0; i < Nz[k]; ++i) ref.emplace_back(z[k][i], k, i);
+        }
+        std::sort(ref.begin(), ref.end());
+        HostLayout Z;
+        build_layout(lb, Nz, z, 1e-3, 2048, 544, 24.0, Z);
+        CHECK(Z.T == (int64_t)ref.size() && Z.T >= (1 << 20));
+        for (int64_t t = 0; t < Z.T; ++t) {
+            CHECK(Z.xm[t] == std::get<0>(ref[t]) && Z.mid[t] == std::get<1>(ref[t]));
+            CHECK(Z.mpos[std::get<1>(ref[t])][std::get<2>(ref[t])] == (uint32_t)t);
+        }
+        int64_t covered = 0;
+        for (int b = 0; b < Z.nt; ++b)
+            for (uint32_t t = Z.tstart[b]; t < Z.tstart[b + 1]; ++t) {
+                CHECK(Z.tile_of[t] == (uint32_t)b);
+                CHECK(Z.pos[t] == (Z.xm[t] - Z.xlb[b]) / 1e-3);
+                ++covered;
+            }
+        CHECK(covered == Z.T);
+
+        // padded stream: tile b's points at toff[b] + (t - tstart[b]); e^{pos},
+        // ephi 1 and the marginal there, and 1 / 0 / 0xff in the padding
+        std::vector<uint32_t> toff(Z.nt);
+        int64_t o = 0;
+        for (int b = 0; b < Z.nt; ++b) {
+            toff[b] = (uint32_t)o;
+            o += ((int64_t)(Z.tstart[b + 1] - Z.tstart[b]) + 15) / 16 * 16;
+        }
+        const size_t Tp = (size_t)o;
+        HVec<float> ep(Tp), ph(Tp);
+        HVec<uint8_t> em(Tp);
+        fill_padded_stream<float>(Z.nt, Z.tstart.data(), toff.data(), Tp, Z.pos.data(), Z.mid.data(), ep.data(),
+                                  ph.data(), em.data());
+        std::vector<char> seen(Tp, 0);
+        for (int b = 0; b < Z.nt; ++b)
+            for (uint32_t t = Z.tstart[b]; t < Z.tstart[b + 1]; ++t) {
+                const size_t u = toff[b] + (t - Z.tstart[b]);
+                CHECK(ep[u] == (float)std::exp(Z.pos[t]) && ph[u] == 1.0f && em[u] == Z.mid[t]);
+                seen[u] = 1;
+            }
+        for (size_t u = 0; u < Tp; ++u)
+            if (!seen[u]) CHECK(ep[u] == 1.0f && ph[u] == 0.0f && em[u] == 0xff);
+        HVec<float> pc(Z.T);
+        convert_parallel(Z.T, Z.pos.data(), pc.data());
+        for (int64_t t = 0; t < Z.T; ++t) CHECK(pc[t] == (float)Z.pos[t]);
+    }
     std::printf("ok\n");
     return 0;
 }

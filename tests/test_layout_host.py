@@ -1,5 +1,7 @@
 """Host logic of the merged-order tiling and the batch layout (csrc/layout.h),
 compiled as a small host program: tie order, tile limits, per-marginal counts,
+the threaded merge above a million points against a plain sort, the padded
+stream of the tile kernels,
 instance offsets and zero decays across instance boundaries."""
 import os
 import shutil
@@ -24,7 +26,7 @@ def test_layout_host(tmp_path):
         pytest.skip("g++ or CUDA headers not available")
     exe = str(tmp_path / "layout_check")
     src = os.path.join(ROOT, "tests", "host", "layout_check.cpp")
-    subprocess.run([cxx, "-std=c++17", "-O1", "-I" + inc,
+    subprocess.run([cxx, "-std=c++17", "-O1", "-pthread", "-I" + inc,
                     "-I" + os.path.join(ROOT, "paper_2405_19246_gb300", "csrc"),
                     "-I" + os.path.join(ROOT, "include"), src, "-o", exe], check=True,
                    capture_output=True, text=True)
