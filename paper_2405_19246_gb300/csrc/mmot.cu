@@ -1022,17 +1022,26 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
                 if (i > 0 && hx[k][i] < hx[k][i - 1])
                     return fail(MMOT_ERR_UNSORTED, "instance %d: x[%d] decreases at index %lld", q, k, (long long)i);
             }
-            long double sum = 0.0L;
+            // compensated (Neumaier) sum: error about one rounding of the
+            // total, far inside the 1e-12 check (a long double sum is
+            // software quad precision on some hosts)
+            double sum = 0.0, comp = 0.0;
             for (int64_t i = 0; i < n; ++i) {
                 const double m = qmu[k][i];
                 if (!(m >= 0.0) || !std::isfinite(m))
                     return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d][%lld] negative or not finite", q, k,
                                 (long long)i);
-                sum += m;
+                const double t = sum + m;
+                comp += (std::fabs(sum) >= std::fabs(m)) ? (sum - t) + m : (m - t) + sum;
+                sum = t;
             }
-            if (!in.Ntot && std::fabs((double)sum - 1.0) > 1e-12)
-                return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, (double)sum);
-            hmu[k].insert(hmu[k].end(), qmu[k].begin(), qmu[k].end());
+            sum += comp;
+            if (!in.Ntot && std::fabs(sum - 1.0) > 1e-12)
+                return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, sum);
+            if (hmu[k].empty())
+                hmu[k] = std::move(qmu[k]);
+            else
+                hmu[k].insert(hmu[k].end(), qmu[k].begin(), qmu[k].end());
             seg_off[(size_t)(q + 1) * l + k] = seg_off[(size_t)q * l + k] + n;
         }
         if (nin == 1) {
@@ -1052,8 +1061,12 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
         }
         HostLayout Lq;
         build_layout(l, in.N, hx, in.eps, K, jcap, limit, Lq);
-        append_layout(L, Lq, &seg_off[(size_t)q * l]);
-        for (int b = 0; b < Lq.nt; ++b) {
+        const int ntq = Lq.nt;
+        if (q == 0)
+            L = std::move(Lq);   // the first instance: appending to an empty layout is the layout itself
+        else
+            append_layout(L, Lq, &seg_off[(size_t)q * l]);
+        for (int b = 0; b < ntq; ++b) {
             hseg.push_back(q);
             hteps.push_back(in.eps);
         }

@@ -77,6 +77,18 @@ int main()
     for (int k = 0; k < l; ++k) off[k] = N[k];
     append_layout(B, Ly, off.data());
     CHECK(B.T == L.T + Ly.T && B.nt == L.nt + Ly.nt);
+    // appending to an empty layout gives the layout itself (plan creation
+    // takes a single instance's layout as it is)
+    {
+        HostLayout E;
+        E.l = l;
+        std::vector<int64_t> zero(l, 0);
+        append_layout(E, L, zero.data());
+        CHECK(E.T == L.T && E.nt == L.nt && E.tstart == L.tstart && E.cnt == L.cnt && E.reftile == L.reftile);
+        CHECK(E.mid == L.mid && E.pos == L.pos && E.tile_of == L.tile_of && E.span == L.span);
+        CHECK(E.xlb == L.xlb && E.xrb == L.xrb && E.ulb == L.ulb && E.urb == L.urb);
+        for (int k = 0; k < l; ++k) CHECK(E.mpos[k] == L.mpos[k]);
+    }
     CHECK(B.tstart.size() == (size_t)B.nt + 1 && B.tstart.back() == (uint32_t)B.T);
     std::vector<int32_t> seg;
     for (int b = 0; b < L.nt; ++b) seg.push_back(0);
