@@ -89,8 +89,10 @@ inline int layout_threads(int64_t T)
     return (int)std::min<unsigned>(16u, std::max(1u, hc));
 }
 
-inline void build_layout(int l, const int64_t *N, const std::vector<std::vector<double>> &hx, double eps,
-                         int K, int jcap, double limit, HostLayout &L)
+// hx[k]: the sorted coordinates of marginal k (any random-access container)
+template <typename XS>
+inline void build_layout(int l, const int64_t *N, const XS &hx, double eps, int K, int jcap, double limit,
+                         HostLayout &L)
 {
     L.l = l;
     int64_t T = 0;

@@ -1001,43 +1001,90 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
     double ugrid_h = 0.0;   // > 0: one uniform grid of step ugrid_h for every marginal
     HostLayout L;
     L.l = l;
-    std::vector<std::vector<double>> hmu(l);
+    std::vector<HVec<double>> hmu(l);
     std::vector<int32_t> hseg;
     std::vector<double> hteps;
     std::vector<int32_t> seg_tile0(1, 0);
     std::vector<int64_t> seg_off((size_t)(nin + 1) * l, 0);   // first local index of instance q in marginal k
     for (int q = 0; q < nin; ++q) {
         const InstanceIn &in = ins[q];
-        std::vector<std::vector<double>> hx(l), qmu(l);
+        std::vector<HVec<double>> hx(l), qmu(l);
+        int64_t Tq = 0;
         for (int k = 0; k < l; ++k) {
             const int64_t n = in.N[k];
+            Tq += n;
             hx[k].resize(n);
             qmu[k].resize(n);
-            const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-            CUDA_TRY(cudaMemcpy(hx[k].data(), in.x[k], sizeof(double) * n, kind));
-            CUDA_TRY(cudaMemcpy(qmu[k].data(), in.mu[k], sizeof(double) * n, kind));
+            if (inputs_on_device) {
+                CUDA_TRY(cudaMemcpy(hx[k].data(), in.x[k], sizeof(double) * n, cudaMemcpyDeviceToHost));
+                CUDA_TRY(cudaMemcpy(qmu[k].data(), in.mu[k], sizeof(double) * n, cudaMemcpyDeviceToHost));
+            }
+        }
+        if (!inputs_on_device) {
+            // host inputs: plain copies, one host thread per marginal for large inputs
+            auto copy_marginal = [&](int k) {
+                std::memcpy(hx[k].data(), in.x[k], sizeof(double) * in.N[k]);
+                std::memcpy(qmu[k].data(), in.mu[k], sizeof(double) * in.N[k]);
+            };
+            if (layout_threads(Tq) > 1)
+                host_parallel(l, copy_marginal);
+            else
+                for (int k = 0; k < l; ++k) copy_marginal(k);
+        }
+        // checks of the marginals (one host thread each for large inputs);
+        // the first failure in marginal order is reported
+        std::vector<mmot_status> kst(l, MMOT_OK);
+        std::vector<std::string> kmsg(l);
+        auto check_marginal = [&](int k) {
+            const int64_t n = in.N[k];
+            char buf[160];
+            const HVec<double> &xk = hx[k], &mk = qmu[k];
             for (int64_t i = 0; i < n; ++i) {
-                if (!std::isfinite(hx[k][i]))
-                    return fail(MMOT_ERR_INVALID_ARG, "instance %d: x[%d][%lld] not finite", q, k, (long long)i);
-                if (i > 0 && hx[k][i] < hx[k][i - 1])
-                    return fail(MMOT_ERR_UNSORTED, "instance %d: x[%d] decreases at index %lld", q, k, (long long)i);
+                if (!std::isfinite(xk[i])) {
+                    std::snprintf(buf, sizeof(buf), "instance %d: x[%d][%lld] not finite", q, k, (long long)i);
+                    kst[k] = MMOT_ERR_INVALID_ARG;
+                    kmsg[k] = buf;
+                    return;
+                }
+                if (i > 0 && xk[i] < xk[i - 1]) {
+                    std::snprintf(buf, sizeof(buf), "instance %d: x[%d] decreases at index %lld", q, k, (long long)i);
+                    kst[k] = MMOT_ERR_UNSORTED;
+                    kmsg[k] = buf;
+                    return;
+                }
             }
             // compensated (Neumaier) sum: error about one rounding of the
             // total, far inside the 1e-12 check (a long double sum is
             // software quad precision on some hosts)
             double sum = 0.0, comp = 0.0;
             for (int64_t i = 0; i < n; ++i) {
-                const double m = qmu[k][i];
-                if (!(m >= 0.0) || !std::isfinite(m))
-                    return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d][%lld] negative or not finite", q, k,
-                                (long long)i);
+                const double m = mk[i];
+                if (!(m >= 0.0) || !std::isfinite(m)) {
+                    std::snprintf(buf, sizeof(buf), "instance %d: mu[%d][%lld] negative or not finite", q, k,
+                                  (long long)i);
+                    kst[k] = MMOT_ERR_INVALID_ARG;
+                    kmsg[k] = buf;
+                    return;
+                }
                 const double t = sum + m;
                 comp += (std::fabs(sum) >= std::fabs(m)) ? (sum - t) + m : (m - t) + sum;
                 sum = t;
             }
             sum += comp;
-            if (!in.Ntot && std::fabs(sum - 1.0) > 1e-12)
-                return fail(MMOT_ERR_INVALID_ARG, "instance %d: mu[%d] sums to %.17g, not 1", q, k, sum);
+            if (!in.Ntot && std::fabs(sum - 1.0) > 1e-12) {
+                std::snprintf(buf, sizeof(buf), "instance %d: mu[%d] sums to %.17g, not 1", q, k, sum);
+                kst[k] = MMOT_ERR_INVALID_ARG;
+                kmsg[k] = buf;
+            }
+        };
+        if (layout_threads(Tq) > 1)
+            host_parallel(l, check_marginal);
+        else
+            for (int k = 0; k < l; ++k) check_marginal(k);
+        for (int k = 0; k < l; ++k)
+            if (kst[k] != MMOT_OK) return fail(kst[k], "%s", kmsg[k].c_str());
+        for (int k = 0; k < l; ++k) {
+            const int64_t n = in.N[k];
             if (hmu[k].empty())
                 hmu[k] = std::move(qmu[k]);
             else
@@ -1278,7 +1325,7 @@ mmot_status plan_build(int l, const std::vector<InstanceIn> &ins, mmot_precision
             const int P = layout_threads(N[k]);
             const int64_t n = N[k];
             std::vector<double> &dst = hlm[k];
-            const std::vector<double> &src = hmu[k];
+            const HVec<double> &src = hmu[k];
             host_parallel(P, [&](int pp) {
                 for (int64_t i = n * pp / P; i < n * (pp + 1) / P; ++i) dst[i] = src[i] > 0 ? std::log(src[i]) : -INFINITY;
             });
