@@ -165,3 +165,34 @@ def test_tile_cap_cache_tunes_each_bucket_once():
     assert bucket_key(c) != bucket_key(a)
     assert cache.cap(a) == 512 and cache.cap(b) == 512 and calls == [3]
     assert cache.cap(c) == 512 and calls == [3, 1]
+
+
+def test_refill_respects_cohort_size_and_budget():
+    """Joins take waiting requests oldest first, at most up to max_cohort
+    active instances and within the freed memory plus the unused budget;
+    the server's and the cohort's memory accounting follow."""
+    import collections
+    reqs = _reqs(6)
+    per = estimate_bytes(reqs[0])
+    srv = Server(check_every=10, mem_budget=5 * per, max_cohort=4,
+                 make_batch=lambda rs: FakeBatch(rs, {r.rid: 10 for r in rs}))
+
+    class C:
+        mem = 4 * per
+
+    srv.used = 4 * per
+    srv.waiting = collections.deque(reqs)
+    # one instance finished (its memory freed), three still active: one joins
+    take = srv._refill(C, per, 3)
+    assert [r.rid for r in take] == [0]
+    assert srv.used == 4 * per and C.mem == 4 * per and srv.joined == 1
+    # two finished, two active: room for 2 + 1 unused, but the cohort caps at 4
+    srv.used = 4 * per
+    C.mem = 4 * per
+    take = srv._refill(C, 2 * per, 2)
+    assert [r.rid for r in take] == [1, 2]
+    assert srv.used == 4 * per and C.mem == 4 * per
+    # nothing freed, budget full: nobody joins
+    srv.used = 5 * per
+    assert srv._refill(C, 0, 1) == []
+    assert [r.rid for r in srv.waiting] == [3, 4, 5]
